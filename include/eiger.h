@@ -1,0 +1,196 @@
+/*
+ * eiger.h -- C ABI of the GB300 runtime-adaptive equi-join library.
+ *
+ * The library implements the join path of "Eiger: An Efficient Library for
+ * GPU-based Data Analytics": it profiles the join keys while the query runs
+ * (min/max and a HyperLogLog++ sketch, Sec. 4 and Sec. 4.1), uses those
+ * statistics to choose between a non-partitioned global-memory hash join and a
+ * radix-partitioned shared-memory hash join and to set their knobs (fanout,
+ * passes, table load factor; Sec. 1, Table 1, Sec. 3.2), and compresses int64
+ * keys on the fly to uint32 offsets from the build-side minimum when the value
+ * range allows (frame-of-reference encoding, Sec. 4.3). The result is the list
+ * of matching tuple-ID pairs (Sec. 2.2, late materialisation via TIDs).
+ *
+ * Names: the paper's R is the build side (the smaller relation), S the probe
+ * side; the join throughput is (|R| + |S|) / time (Sec. 5.2).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers prefixed d_ are device memory owned by the caller. The library
+ *    never allocates, frees or retains them beyond the call.
+ *  - Scratch memory ("workspace") is supplied by the caller; its size comes
+ *    from the matching *_workspace query. Contents need not be initialised and
+ *    are garbage after the call.
+ *  - `stream` is a CUDA stream handle (cudaStream_t / CUstream) passed as
+ *    void*; NULL means the legacy default stream. Work is enqueued on it.
+ *    Calls that return host-side results (statistics, match counts)
+ *    synchronise that stream before returning.
+ *  - Row counts are int64. Build and probe sizes must each be < 2^32 (the
+ *    output tuple IDs are uint32); larger inputs return EIGER_ERR_INVALID_ARG.
+ *  - No CPU fallback exists: every step runs in the library's CUDA kernels. A
+ *    CUDA failure returns EIGER_ERR_CUDA with the message in
+ *    eiger_last_error().
+ *  - Errors leave caller buffers in an unspecified state but never write past
+ *    the sizes given. The library stays usable after any error status.
+ */
+#ifndef EIGER_H
+#define EIGER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EIGER_OK = 0,
+    EIGER_ERR_INVALID_ARG = 1, /* bad pointer/size/dtype/knob combination          */
+    EIGER_ERR_CAPACITY = 2,    /* more matches than `capacity`; *out_count = needed  */
+    EIGER_ERR_WORKSPACE = 3,   /* workspace smaller than the *_workspace query says */
+    EIGER_ERR_TABLE_FULL = 4,  /* a hash-table probe sequence hit its iteration cap  */
+    EIGER_ERR_CUDA = 5,        /* a CUDA runtime call or kernel launch failed        */
+    EIGER_ERR_INTERNAL = 6     /* a device-side consistency check failed             */
+} eiger_status;
+
+typedef enum { EIGER_I32 = 0, EIGER_I64 = 1 } eiger_dtype;
+
+/* Join variants (Sec. 3.2; Table 1 lists the runtime properties that choose). */
+typedef enum {
+    EIGER_AUTO = 0,   /* statistics -> planner -> one of NPHJ / PHJ1 / PHJ2           */
+    EIGER_NPHJ = 1,   /* non-partitioned hash join, global-memory open addressing    */
+    EIGER_PHJ1 = 2,   /* radix-partitioned hash join, 1 partitioning pass            */
+    EIGER_PHJ2 = 3,   /* radix-partitioned hash join, 2 partitioning passes          */
+    EIGER_STATIC = 4  /* the plain static method: NPHJ with no statistics, no
+                         narrowing, load factor 0.5 (the single fixed choice the
+                         paper contrasts with adaptivity, Sec. 1 and Sec. 3.2)      */
+} eiger_variant;
+
+#define EIGER_HLL_P 14
+#define EIGER_HLL_M 16384 /* 2^EIGER_HLL_P registers */
+
+/* Column statistics (Sec. 4: min/max; Sec. 4.1: HyperLogLog++ NDV estimate). */
+typedef struct {
+    int64_t n;        /* rows profiled                                          */
+    int64_t min;      /* signed minimum; INT64_MAX when n == 0                   */
+    int64_t max;      /* signed maximum; INT64_MIN when n == 0                   */
+    double estimate;  /* distinct-value estimate from the registers; 0 when n==0 */
+    uint8_t hll[EIGER_HLL_M]; /* dense registers, each the max rank seen (0..51) */
+} eiger_stats_t;
+
+/* A join plan: the variant and its knobs (Sec. 1 "knob tuning"). */
+typedef struct {
+    int32_t variant;     /* EIGER_NPHJ, EIGER_PHJ1, EIGER_PHJ2 or EIGER_STATIC       */
+    int32_t bits1;       /* PHJ: radix bits of pass 1 (1..12)                        */
+    int32_t bits2;       /* PHJ2: radix bits of pass 2 (1..12); 0 for PHJ1           */
+    int32_t narrow;      /* 1: keys stored as uint32 offsets from key_min            */
+    float load_factor;   /* NPHJ: build rows / table slots, in (0, 0.9]              */
+    int32_t selector;    /* who chose: 0 rules, 1 learned model, 2 caller knobs,
+                            3 static                                                 */
+    int64_t key_min;     /* build-side min/max the plan was made from (filled in by  */
+    int64_t key_max;     /* the library; ignored on input)                           */
+} eiger_plan_t;
+
+/*
+ * Scratch bytes eiger_stats needs for a column of n rows of `dtype`.
+ * Errors: INVALID_ARG for n < 0, a bad dtype or bytes == NULL.
+ */
+eiger_status eiger_stats_workspace(int64_t n, eiger_dtype dtype, size_t* bytes);
+
+/*
+ * eiger_stats -- profile one key column (Sec. 4, Sec. 4.1).
+ * d_keys:  n keys of `dtype` (int32 or int64), contiguous, any alignment.
+ *          An int32 key and the same value as int64 hash identically.
+ * out:     host struct; receives n, min, max, the 2^14 HyperLogLog registers and
+ *          the estimate. Register update: h = SplitMix64 output function of the
+ *          64-bit key; index = top 14 bits of h; rank = 1 + leading zeros of the
+ *          remaining 50 bits (51 when they are all zero); register = max rank.
+ *          Estimate: the HyperLogLog raw estimate alpha_m m^2 / sum 2^-reg with
+ *          linear counting m ln(m/V) when V zero registers remain and the raw
+ *          estimate is <= 2.5 m; no bias tables (64-bit hash, no large-range
+ *          correction).
+ * Synchronises `stream`. n == 0 is legal (see eiger_stats_t).
+ * Errors: INVALID_ARG (NULL out, NULL keys with n > 0, n < 0, bad dtype),
+ *         WORKSPACE, CUDA.
+ */
+eiger_status eiger_stats(const void* d_keys, int64_t n, eiger_dtype dtype, eiger_stats_t* out,
+                         void* d_workspace, size_t ws_bytes, void* stream);
+
+/*
+ * eiger_plan -- the rule-based selector and knob tuner (Sec. 1: statistics drive
+ * algorithm selection and knob tuning; Table 1: relation cardinalities and the
+ * key distribution decide). Host-only; launches nothing, needs no GPU.
+ * build/probe: statistics of the two key columns (probe may be NULL: only its
+ *          size np is then used).
+ * out:     the chosen plan (variant never EIGER_AUTO; selector = 0).
+ * Errors: INVALID_ARG.
+ */
+eiger_status eiger_plan(const eiger_stats_t* build, const eiger_stats_t* probe, int64_t nb,
+                        int64_t np, eiger_dtype dtype, eiger_plan_t* out);
+
+/*
+ * Scratch bytes eiger_join / eiger_join_sum need. `variant` and `knobs` as
+ * passed to the join; for EIGER_AUTO (or knobs == NULL with a non-static
+ * variant) the result covers every plan the selector can return.
+ * Errors: INVALID_ARG.
+ */
+eiger_status eiger_join_workspace(int64_t nb, int64_t np, eiger_dtype dtype, eiger_variant variant,
+                                  const eiger_plan_t* knobs, size_t* bytes);
+
+/*
+ * eiger_join -- equi-join R (build) with S (probe) on one key column
+ * (Sec. 3.2), emitting every matching pair of tuple IDs.
+ * d_bkeys, nb:  build keys (dtype), nb rows.  d_pkeys, np: probe keys.
+ * d_bpay, d_ppay, payload_bytes: optional payload columns (4 or 8 bytes per
+ *          row; NULL when absent). They are read only when the matching
+ *          d_out_*pay output is requested (gather by tuple ID, Sec. 3.2 GFUR).
+ * variant: EIGER_AUTO runs eiger_stats on the build keys, then eiger_plan,
+ *          then the chosen variant. NPHJ/PHJ1/PHJ2 also profile the build keys
+ *          (narrowing and the probe range test need min/max) and take their
+ *          knobs from `knobs` when non-NULL (bits1/bits2/narrow/load_factor),
+ *          else from the planner. EIGER_STATIC profiles nothing.
+ * Outputs (each NULL or an array of `capacity` elements, at least one given):
+ *          d_out_bidx / d_out_pidx: uint32 build / probe row of each match;
+ *          d_out_bpay / d_out_ppay: the matching rows' payloads (payload_bytes
+ *          wide). Match k is entry k of every given array. Order unspecified.
+ * out_count: host; receives |J|, the number of matches.
+ * capacity: entries available per output array. If |J| > capacity the call
+ *          returns EIGER_ERR_CAPACITY, *out_count = |J|, and at most capacity
+ *          entries are written (capacity = 0 is a count-only query).
+ * plan_used: host, nullable; receives the plan that ran (with key_min/max).
+ * Synchronises `stream` (statistics readback and the final count).
+ * Errors: INVALID_ARG, CAPACITY, WORKSPACE, TABLE_FULL, CUDA, INTERNAL.
+ */
+eiger_status eiger_join(eiger_dtype dtype, const void* d_bkeys, const void* d_bpay, int64_t nb,
+                        const void* d_pkeys, const void* d_ppay, int64_t np, int32_t payload_bytes,
+                        eiger_variant variant, const eiger_plan_t* knobs, uint32_t* d_out_bidx,
+                        uint32_t* d_out_pidx, void* d_out_bpay, void* d_out_ppay,
+                        int64_t capacity, int64_t* out_count, void* d_workspace, size_t ws_bytes,
+                        eiger_plan_t* plan_used, void* stream);
+
+/*
+ * eiger_join_sum -- the join fused with an exact aggregate instead of
+ * materialised pairs: sum over matches (i, j) of build_pay[i] + probe_pay[j]
+ * (payloads sign-extended to 64 bits), accumulated modulo 2^64 and returned as
+ * int64; addition modulo 2^64 is exact and order-independent. This is the
+ * foreign-key join whose matched payloads are summed (the star-schema workload
+ * shape of the TPC-H joins, Sec. 5.7). Payloads are required. Arguments otherwise as eiger_join.
+ * out_sum, out_count: host.
+ * Errors: as eiger_join except CAPACITY.
+ */
+eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* d_bpay, int64_t nb,
+                            const void* d_pkeys, const void* d_ppay, int64_t np,
+                            int32_t payload_bytes, eiger_variant variant, const eiger_plan_t* knobs,
+                            int64_t* out_sum, int64_t* out_count, void* d_workspace,
+                            size_t ws_bytes, eiger_plan_t* plan_used, void* stream);
+
+/* Message of the last non-OK status returned on the calling host thread. */
+const char* eiger_last_error(void);
+
+/* Version string of the library build. */
+const char* eiger_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EIGER_H */
