@@ -1,0 +1,393 @@
+"""Benchmark of the adaptive equi-join on GB300.
+
+One step = one eiger_join(AUTO) call on resident device inputs: build-side
+statistics (min/max + HyperLogLog++), plan, radix partitioning of both sides,
+the shared-memory join, and the match count readback. The workload is the
+variant-sweep join at nb = 2^26 unique dense int64 build keys (span < 2^32, so
+keys narrow to uint32) and np = 2^28 probe keys drawn uniformly from them;
+output = the 2^28 (build_idx, probe_idx) pairs. Inputs (2.5 GB) exceed the L2
+cache, so no flush is needed between steps.
+
+Also measured, on the same inputs: the static hash join (no statistics, no
+narrowing, no partitioning: the single fixed method) and the end-to-end call
+from pinned host buffers (keys copied in, pairs copied out, every step). The
+roofline line takes the dominant stage's algorithmic bytes over its device
+time, both from the library's per-launch CUDA events in the timed region.
+
+Multi-GPU: replicas only (each rank joins its own seeded copy; no collective
+on the data path); value = all ranks' tuples / the slowest rank's time.
+
+``--impl reference`` times the CPU oracle (the unordered_multimap join plus
+canonical sort) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "join tuples/s and HBM GB/s vs peak: adaptive vs static hash join"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["eiger", "reference"], default="eiger")
+    ap.add_argument("--log2-nb", type=int, default=26)
+    ap.add_argument("--ratio", type=int, default=4)
+    ap.add_argument("--keys", choices=["dense", "random"], default="dense")
+    ap.add_argument("--theta", type=float, default=0.0)
+    ap.add_argument("--variant", default="auto")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-static", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest value over ranks (the slowest rank's time); identity for 1 rank."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.rows = []
+        self.proc = None
+        self.target = None
+        try:
+            import torch
+
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.target = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            self.target = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.target:
+            cmd += ["-i", self.target]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        num = lambda x: float(x) if x.replace(".", "", 1).isdigit() else float("nan")
+        sm = [num(r[1]) for r in rows]
+        mx = [num(r[2]) for r in rows]
+        loaded = [s for s, r in zip(sm, rows) if num(r[3]) > 200] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i - 5] for r in rows for i in range(5, 9)
+                          if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "samples": len(rows),
+                "power_w_max": max(num(r[3]) for r in rows), "reasons": reasons}
+
+
+def workload_desc(args):
+    nb = 1 << args.log2_nb
+    return (f"variant_sweep join: nb=2^{args.log2_nb} unique {args.keys} int64 build keys, "
+            f"np={args.ratio}*nb probe keys drawn from them (zipf theta={args.theta}), "
+            f"output (build_idx, probe_idx) pairs"), nb, nb * args.ratio
+
+
+def cpu_oracle_sample(args, min_seconds=10.0):
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    from paper_2607_04489_gb300 import workloads
+
+    log2 = min(args.log2_nb, 20)
+    w = workloads.variant_sweep(1 << log2, args.ratio, keys=args.keys, theta=args.theta, seed=0,
+                                device="cpu", payload_bytes=8)
+    bk, pk = w.build_keys.numpy(), w.probe_keys.numpy()
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.join(bk, pk)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or runs >= 8:
+            break
+    tput = runs * (bk.size + pk.size) / el
+    return {"value": tput, "unit": "tuples/s", "cores": 1, "kind": "oracle",
+            "sample": f"nb=2^{log2}, np={args.ratio}*2^{log2}, same key/probe distribution; "
+                      f"{runs} run(s) of the full join with canonical pair sort in {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2607_04489_gb300 import workloads
+
+    desc, nb, np_ = workload_desc(args)
+    log2 = min(args.log2_nb, 20)
+    w = workloads.variant_sweep(1 << log2, args.ratio, keys=args.keys, theta=args.theta, seed=0,
+                                device="cpu", payload_bytes=8)
+    bk, pk = w.build_keys.numpy(), w.probe_keys.numpy()
+    for _ in range(args.warmup):
+        oracle.join(bk, pk)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.join(bk, pk)
+    el = time.perf_counter() - t0
+    tput = args.steps * (bk.size + pk.size) / el
+    sample = f"nb=2^{log2}, np={args.ratio}*2^{log2} per step (bounded sample of the workload)"
+    line = {"impl": "reference", "metric": METRIC, "value": tput, "unit": "tuples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": desc, "nb": nb, "np": np_},
+            "cpu_baseline": {"value": tput, "unit": "tuples/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": tput, "unit": "tuples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_eiger(args):
+    import torch
+
+    from paper_2607_04489_gb300 import eiger, workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    eiger.load()
+    desc, nb, np_ = workload_desc(args)
+    w = workloads.variant_sweep(nb, args.ratio, keys=args.keys, theta=args.theta, seed=rank,
+                                device=dev, payload_bytes=8)
+    w.build_pay = w.probe_pay = None
+    torch.cuda.empty_cache()
+    bk, pk = w.build_keys, w.probe_keys
+    out_b = torch.empty(np_, dtype=torch.int32, device=dev)
+    out_p = torch.empty(np_, dtype=torch.int32, device=dev)
+    ws = torch.empty(eiger.join_workspace(nb, np_, eiger.I64, args.variant), dtype=torch.uint8,
+                     device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(variant, workspace):
+        st, cnt, plan = eiger.join_into(bk, pk, variant=variant, out_bidx=out_b, out_pidx=out_p,
+                                        capacity=np_, workspace=workspace, stream=stream)
+        if st != eiger.OK or cnt != np_:
+            raise RuntimeError(f"join failed: status {st}, count {cnt}: {eiger.last_error()}")
+        return plan
+
+    # ---- adaptive join: warm-up, then the timed region with per-launch events
+    for _ in range(args.warmup):
+        plan = step(args.variant, ws)
+    eiger.profile(True)
+    stages = {}
+    launches = 0
+    sampler = ClockSampler(local).start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan = step(args.variant, ws)
+        for name, ms, nl, by in eiger.profile_read():
+            s = stages.setdefault(name, [0.0, 0.0, 0])
+            s[0] += ms
+            s[1] += by
+            s[2] += 1
+            launches += nl
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = sampler.stop()
+    eiger.profile(False)
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    tuples = world * (nb + np_)
+    value = tuples / (ms_step * 1e-3)
+
+    # ---- the static hash join on the same inputs
+    static = None
+    if not args.no_static:
+        del ws
+        torch.cuda.empty_cache()
+        ws_s = torch.empty(eiger.join_workspace(nb, np_, eiger.I64, "static"), dtype=torch.uint8,
+                           device=dev)
+        for _ in range(args.warmup):
+            step("static", ws_s)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step("static", ws_s)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        sms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        static = {"value": tuples / (sms * 1e-3), "unit": "tuples/s", "ms_per_step": sms,
+                  "speedup_of_adaptive": sms / ms_step}
+        del ws_s
+        torch.cuda.empty_cache()
+        ws = torch.empty(eiger.join_workspace(nb, np_, eiger.I64, args.variant), dtype=torch.uint8,
+                         device=dev)
+
+    # ---- end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hb = bk.cpu().pin_memory()
+        hp = pk.cpu().pin_memory()
+        hob = torch.empty(np_, dtype=torch.int32).pin_memory()
+        hop = torch.empty(np_, dtype=torch.int32).pin_memory()
+        dbk = torch.empty_like(bk)
+        dpk = torch.empty_like(pk)
+
+        def e2e_step():
+            dbk.copy_(hb, non_blocking=True)
+            dpk.copy_(hp, non_blocking=True)
+            st, cnt, _ = eiger.join_into(dbk, dpk, variant=args.variant, out_bidx=out_b,
+                                         out_pidx=out_p, capacity=np_, workspace=ws, stream=stream)
+            if st != eiger.OK or cnt != np_:
+                raise RuntimeError(f"join failed: {eiger.last_error()}")
+            hob.copy_(out_b, non_blocking=True)
+            hop.copy_(out_p, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        e2e = {"value": tuples / (ems * 1e-3), "unit": "tuples/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": int(bk.numel() * 8 + pk.numel() * 8),
+               "d2h_bytes_per_step": int(2 * 4 * np_)}
+
+    # ---- roofline of the dominant stage
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    stage_rows = []
+    for name, (ms_tot, by_tot, cnt) in stages.items():
+        ms_avg = ms_tot / cnt
+        by_avg = by_tot / cnt
+        stage_rows.append({"stage": name, "ms": round(ms_avg, 4), "bytes": by_avg,
+                           "gbs": by_avg / (ms_avg * 1e-3) / 1e9 if ms_avg > 0 else None})
+    stage_rows.sort(key=lambda r: -r["ms"])
+    dom = stage_rows[0]
+    compulsory = nb * 8 + np_ * 8 + np_ * 8  # keys in, pairs out
+    line = {
+        "metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": desc, "nb": nb, "np": np_, "keys": args.keys, "theta": args.theta,
+                   "variant": args.variant, "l2": "inputs (2.5 GB) larger than L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "hbm_gbs_compulsory": compulsory / (ms_step * 1e-3) / 1e9,
+        "plan": {"variant": plan.variant, "bits1": plan.bits1, "bits2": plan.bits2,
+                 "narrow": plan.narrow, "load_factor": plan.load_factor},
+        "roofline": {"bound": "hbm", "kernel": dom["stage"], "achieved": dom["gbs"], "peak": hbm,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": dom["gbs"] / hbm,
+                     "traffic": None},
+        "stages": stage_rows,
+        "gpu_launches": launches,
+        "static": static,
+        "e2e": e2e,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample(args)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_eiger(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

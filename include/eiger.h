@@ -183,6 +183,33 @@ eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* 
                             int64_t* out_sum, int64_t* out_count, void* d_workspace,
                             size_t ws_bytes, eiger_plan_t* plan_used, void* stream);
 
+/* One timed stage (one kernel launch, or the three of a scan) of the last
+   call (see eiger_profile). */
+typedef struct {
+    char name[32];    /* stage name, e.g. "part_scatter.p1.probe"              */
+    float ms;         /* device time between CUDA events around the stage     */
+    int32_t launches; /* kernels the stage launched (1, or 3 for a scan)      */
+    double bytes;     /* algorithmic bytes the stage must move (reads of its
+                         inputs plus writes of its outputs, no re-reads)      */
+} eiger_stage_t;
+
+/*
+ * eiger_profile -- per-launch timing for the calling host thread (the
+ * paper's per-kernel breakdowns, Tables of Sec. 5.5-5.6, are this kind of
+ * measurement). When enabled, every kernel launch of the following calls is
+ * bracketed by CUDA events recorded on the call's stream; the records of the
+ * most recent call are kept until the next call. Never fails.
+ */
+eiger_status eiger_profile(int enable);
+
+/*
+ * eiger_profile_read -- copies up to max_stages records of the most recent
+ * call on this thread into `out` (host array) and returns how many the call
+ * made (out == NULL: only the count). The call's stream must have completed
+ * (every join/stats call synchronises it before returning).
+ */
+int eiger_profile_read(eiger_stage_t* out, int max_stages);
+
 /* Message of the last non-OK status returned on the calling host thread. */
 const char* eiger_last_error(void);
 

@@ -1,0 +1,503 @@
+// C ABI of libeiger (declared in include/eiger.h): argument validation,
+// workspace carving, the statistics -> plan -> variant pipeline, and the
+// mapping of CUDA and device-side errors to statuses.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "kernels.cuh"
+#include "planner.h"
+
+namespace eiger {
+
+cudaError_t current_device_info(DevInfo* out) {
+    static std::mutex mu;
+    static DevInfo cache[64];
+    static bool have[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && have[dev]) {
+        *out = cache[dev];
+        return cudaSuccess;
+    }
+    DevInfo d;
+    d.dev = dev;
+    if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&d.l2_bytes, cudaDevAttrL2CacheSize, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&d.max_threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) !=
+        cudaSuccess)
+        return e;
+    if (dev >= 0 && dev < 64) {
+        cache[dev] = d;
+        have[dev] = true;
+    }
+    *out = d;
+    return cudaSuccess;
+}
+
+}  // namespace eiger
+
+using namespace eiger;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+eiger_status fail(eiger_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+eiger_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(EIGER_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define EIGER_CUDA(call, where)                          \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+constexpr int64_t kMaxRows = 0xFFFFFFFFll;  // rows < 2^32: tuple IDs are uint32
+
+size_t l2_bytes_or_default() {
+    DevInfo di;
+    if (current_device_info(&di) == cudaSuccess && di.l2_bytes > 0) return (size_t)di.l2_bytes;
+    cudaGetLastError();
+    return (size_t)126 << 20;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+eiger_status run_stats(const void* keys, int64_t n, int dtype, const StatsScratch& ss,
+                       cudaStream_t stream, eiger_stats_t* out) {
+    out->n = n;
+    if (n == 0) {
+        out->min = INT64_MAX;
+        out->max = INT64_MIN;
+        std::memset(out->hll, 0, sizeof out->hll);
+        out->estimate = 0.0;
+        return EIGER_OK;
+    }
+    EIGER_CUDA(stats_launch(keys, n, dtype, ss, stream), "statistics kernels");
+    static thread_local StatsDev host;
+    EIGER_CUDA(cudaMemcpyAsync(&host, ss.out, sizeof(StatsDev), cudaMemcpyDeviceToHost, stream),
+               "statistics readback");
+    EIGER_CUDA(cudaStreamSynchronize(stream), "statistics synchronise");
+    out->min = host.mn;
+    out->max = host.mx;
+    std::memcpy(out->hll, host.regs, sizeof out->hll);
+    for (int j = 0; j < kHllM; ++j)
+        if (out->hll[j] > kRhoMax) return fail(EIGER_ERR_INTERNAL, "register %d holds %d", j, out->hll[j]);
+    out->estimate = hll_estimate(out->hll);
+    return EIGER_OK;
+}
+
+bool narrowable(int dtype, int64_t nb, int64_t mn, int64_t mx) {
+    if (nb == 0) return false;
+    if (dtype == EIGER_I32) return true;
+    return (uint64_t)mx - (uint64_t)mn <= 0xFFFFFFFFull;
+}
+
+eiger_plan_t static_plan() {
+    eiger_plan_t p{};
+    p.variant = EIGER_STATIC;
+    p.load_factor = 0.5f;
+    p.narrow = 0;
+    p.selector = 3;
+    return p;
+}
+
+PlanDev to_dev(const eiger_plan_t& p, int dtype, const eiger_stats_t* bst) {
+    PlanDev d{};
+    d.variant = p.variant;
+    d.bits1 = p.bits1;
+    d.bits2 = p.bits2;
+    d.narrow = p.narrow;
+    d.key32 = dtype == EIGER_I32 || p.narrow;
+    d.load_factor = p.load_factor;
+    d.dtype = dtype;
+    if (bst) {
+        d.range.lo = bst->min;
+        d.range.hi = bst->max;
+        d.range.offset = d.key32 ? (uint64_t)bst->min : 0ull;
+        d.check_range = 1;
+    } else {
+        d.range.lo = INT64_MIN;
+        d.range.hi = INT64_MAX;
+        d.range.offset = 0;
+        d.check_range = 0;
+    }
+    return d;
+}
+
+// Checks a plan's knobs; `narrow_ok` says whether the build keys allow it.
+eiger_status check_plan(const eiger_plan_t& p, int64_t nb, int dtype, bool narrow_ok) {
+    switch (p.variant) {
+        case EIGER_NPHJ:
+        case EIGER_STATIC: {
+            if (!(p.load_factor > 0.0f && p.load_factor <= 0.9f))
+                return fail(EIGER_ERR_INVALID_ARG, "load_factor %g outside (0, 0.9]", p.load_factor);
+            const bool key32 = dtype == EIGER_I32 || p.narrow;
+            if (key32 && table_slots(nb, p.load_factor) > (1ull << 32))
+                return fail(EIGER_ERR_INVALID_ARG, "hash table of %lld rows needs more than 2^32 slots",
+                            (long long)nb);
+            break;
+        }
+        case EIGER_PHJ1:
+            if (p.bits1 < 1 || p.bits1 > kMaxBits)
+                return fail(EIGER_ERR_INVALID_ARG, "bits1 %d outside [1, %d]", p.bits1, kMaxBits);
+            break;
+        case EIGER_PHJ2:
+            if (p.bits1 < 1 || p.bits1 > kMaxBits || p.bits2 < 1 || p.bits2 > kMaxBits ||
+                p.bits1 + p.bits2 > 20)
+                return fail(EIGER_ERR_INVALID_ARG, "bits (%d, %d) outside [1, %d] each, sum <= 20",
+                            p.bits1, p.bits2, kMaxBits);
+            break;
+        default:
+            return fail(EIGER_ERR_INVALID_ARG, "plan variant %d is not NPHJ/PHJ1/PHJ2/STATIC", p.variant);
+    }
+    if (p.narrow != 0 && p.narrow != 1) return fail(EIGER_ERR_INVALID_ARG, "narrow must be 0 or 1");
+    if (p.narrow && !narrow_ok)
+        return fail(EIGER_ERR_INVALID_ARG, "narrow = 1 but the build key range spans >= 2^32");
+    return EIGER_OK;
+}
+
+struct Layout {
+    Ctrl* ctrl;
+    StatsScratch stats;
+    size_t fixed_end;
+};
+
+Layout fixed_layout(Carve& c) {
+    Layout l;
+    l.ctrl = c.take<Ctrl>(1);
+    l.stats = stats_layout(c);
+    l.fixed_end = c.off;
+    return l;
+}
+
+size_t variant_bytes(Carve c, int64_t nb, int64_t np, const PlanDev& pd, NphjScratch* ns,
+                     PhjScratch* ps) {
+    if (pd.variant == EIGER_NPHJ || pd.variant == EIGER_STATIC) {
+        NphjScratch s = nphj_layout(c, nb, pd);
+        if (ns) *ns = s;
+    } else {
+        PhjScratch s = phj_layout(c, nb, np, pd);
+        if (ps) *ps = s;
+    }
+    return c.off;
+}
+
+struct JoinCall {
+    int dtype;
+    const void* bkeys;
+    const void* bpay;
+    int64_t nb;
+    const void* pkeys;
+    const void* ppay;
+    int64_t np;
+    int pay_bytes;
+    int variant;
+    const eiger_plan_t* knobs;
+    JoinOut out;
+    int64_t* out_count;
+    int64_t* out_sum;
+    void* ws;
+    size_t ws_bytes;
+    eiger_plan_t* plan_used;
+    cudaStream_t stream;
+};
+
+eiger_status validate_common(const JoinCall& c) {
+    if (c.dtype != EIGER_I32 && c.dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype %d", c.dtype);
+    if (c.nb < 0 || c.np < 0 || c.nb > kMaxRows || c.np > kMaxRows)
+        return fail(EIGER_ERR_INVALID_ARG, "row counts must be in [0, 2^32): nb=%lld np=%lld",
+                    (long long)c.nb, (long long)c.np);
+    const size_t kb = c.dtype == EIGER_I32 ? 4 : 8;
+    if ((c.nb > 0 && !c.bkeys) || (c.np > 0 && !c.pkeys))
+        return fail(EIGER_ERR_INVALID_ARG, "NULL key column with rows");
+    if ((c.bkeys && !aligned(c.bkeys, kb)) || (c.pkeys && !aligned(c.pkeys, kb)))
+        return fail(EIGER_ERR_INVALID_ARG, "key columns must be aligned to their element size");
+    const bool pay_used = c.bpay || c.ppay || c.out.bpay_out || c.out.ppay_out || c.out.aggregate;
+    if (pay_used && c.pay_bytes != 4 && c.pay_bytes != 8)
+        return fail(EIGER_ERR_INVALID_ARG, "payload_bytes must be 4 or 8, got %d", c.pay_bytes);
+    if (pay_used) {
+        const size_t pb = (size_t)c.pay_bytes;
+        if ((c.bpay && !aligned(c.bpay, pb)) || (c.ppay && !aligned(c.ppay, pb)) ||
+            (c.out.bpay_out && !aligned(c.out.bpay_out, pb)) || (c.out.ppay_out && !aligned(c.out.ppay_out, pb)))
+            return fail(EIGER_ERR_INVALID_ARG, "payload arrays must be aligned to payload_bytes");
+    }
+    if ((c.out.bpay_out && !c.bpay) || (c.out.ppay_out && !c.ppay))
+        return fail(EIGER_ERR_INVALID_ARG, "payload output requested without its payload column");
+    if ((c.out.bidx && !aligned(c.out.bidx, 4)) || (c.out.pidx && !aligned(c.out.pidx, 4)))
+        return fail(EIGER_ERR_INVALID_ARG, "index outputs must be 4-byte aligned");
+    if (c.variant < EIGER_AUTO || c.variant > EIGER_STATIC)
+        return fail(EIGER_ERR_INVALID_ARG, "bad variant %d", c.variant);
+    if (!c.out_count) return fail(EIGER_ERR_INVALID_ARG, "out_count is NULL");
+    if (!c.ws && c.ws_bytes) return fail(EIGER_ERR_INVALID_ARG, "NULL workspace with nonzero size");
+    return EIGER_OK;
+}
+
+// Resolves the plan. `bst` holds the build statistics (NULL for STATIC).
+eiger_status resolve_plan(const JoinCall& c, const eiger_stats_t* bst, eiger_plan_t* pub) {
+    if (c.variant == EIGER_STATIC) {
+        *pub = static_plan();
+        return check_plan(*pub, c.nb, c.dtype, false);
+    }
+    const bool nok = narrowable(c.dtype, c.nb, bst->min, bst->max);
+    if (c.knobs) {
+        *pub = *c.knobs;
+        if (c.variant != EIGER_AUTO) pub->variant = c.variant;
+        if (pub->variant == EIGER_STATIC)
+            return fail(EIGER_ERR_INVALID_ARG, "use variant EIGER_STATIC, not a STATIC knob plan");
+        pub->selector = 2;
+    } else {
+        *pub = plan_rules(c.variant, c.nb, c.np, c.dtype, nok, l2_bytes_or_default());
+    }
+    if (c.dtype == EIGER_I32) pub->narrow = 1;  // int32 keys always travel as 32-bit offsets
+    eiger_status s = check_plan(*pub, c.nb, c.dtype, nok);
+    if (s != EIGER_OK) return s;
+    pub->key_min = bst->min;
+    pub->key_max = bst->max;
+    return EIGER_OK;
+}
+
+eiger_status run_join(const JoinCall& c) {
+    eiger_status s = validate_common(c);
+    if (s != EIGER_OK) return s;
+    prof_reset();
+    Carve carve{static_cast<char*>(c.ws), 0};
+    Layout lay = fixed_layout(carve);
+    if (lay.fixed_end > c.ws_bytes)
+        return fail(EIGER_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", c.ws_bytes, lay.fixed_end);
+
+    static thread_local eiger_stats_t bst;
+    const bool adaptive = c.variant != EIGER_STATIC;
+    if (adaptive) {
+        s = run_stats(c.bkeys, c.nb, c.dtype, lay.stats, c.stream, &bst);
+        if (s != EIGER_OK) return s;
+    }
+    eiger_plan_t pub;
+    s = resolve_plan(c, adaptive ? &bst : nullptr, &pub);
+    if (s != EIGER_OK) return s;
+    if (c.plan_used) *c.plan_used = pub;
+
+    *c.out_count = 0;
+    if (c.out_sum) *c.out_sum = 0;
+    if (c.nb == 0 || c.np == 0) return EIGER_OK;
+
+    const PlanDev pd = to_dev(pub, c.dtype, adaptive ? &bst : nullptr);
+    NphjScratch ns{};
+    PhjScratch ps{};
+    const size_t need = variant_bytes(carve, c.nb, c.np, pd, &ns, &ps);
+    if (need > c.ws_bytes)
+        return fail(EIGER_ERR_WORKSPACE, "workspace %zu bytes < %zu needed for this plan", c.ws_bytes, need);
+    // Host-side fault injection for tests: EIGER_FAULT=table_full shrinks the
+    // non-partitioned table to 64 slots, so inserts and probes exhaust their
+    // bounded probe sequences and the device error flag path is exercised.
+    const char* fault = std::getenv("EIGER_FAULT");
+    if (fault && std::strcmp(fault, "table_full") == 0 &&
+        (pd.variant == EIGER_NPHJ || pd.variant == EIGER_STATIC))
+        ns.slots = 64;
+
+    EIGER_CUDA(cudaMemsetAsync(lay.ctrl, 0, sizeof(Ctrl), c.stream), "control block reset");
+    const JoinArgs a{c.bkeys, c.nb, c.pkeys, c.np};
+    if (pd.variant == EIGER_NPHJ || pd.variant == EIGER_STATIC)
+        EIGER_CUDA(nphj_run(a, pd, ns, c.out, lay.ctrl, c.stream), "non-partitioned join");
+    else
+        EIGER_CUDA(phj_run(a, pd, ps, c.out, lay.ctrl, c.stream), "partitioned join");
+
+    Ctrl h;
+    EIGER_CUDA(cudaMemcpyAsync(&h, lay.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c.stream),
+               "result readback");
+    EIGER_CUDA(cudaStreamSynchronize(c.stream), "join synchronise");
+    if (h.err & kErrTableFull) return fail(EIGER_ERR_TABLE_FULL, "a hash-table probe sequence hit its cap");
+    if (h.err & kErrInternal) return fail(EIGER_ERR_INTERNAL, "device consistency check failed");
+    prof_set_matches(h.cursor);
+    *c.out_count = (int64_t)h.cursor;
+    if (c.out_sum) *c.out_sum = (int64_t)h.sum;
+    if (!c.out.aggregate && h.cursor > c.out.capacity)
+        return fail(EIGER_ERR_CAPACITY, "%llu matches exceed capacity %llu", h.cursor, c.out.capacity);
+    return EIGER_OK;
+}
+
+size_t join_workspace_bytes(int64_t nb, int64_t np, int dtype, int variant, const eiger_plan_t* knobs) {
+    Carve c{nullptr, 0};
+    fixed_layout(c);
+    size_t best = c.off;
+    auto consider = [&](const eiger_plan_t& p) {
+        PlanDev pd{};
+        pd.variant = p.variant;
+        pd.bits1 = p.bits1;
+        pd.bits2 = p.bits2;
+        pd.narrow = p.narrow;
+        pd.key32 = dtype == EIGER_I32 || p.narrow;
+        pd.load_factor = p.load_factor;
+        pd.dtype = dtype;
+        const size_t b = variant_bytes(c, nb, np, pd, nullptr, nullptr);
+        if (b > best) best = b;
+    };
+    if (variant == EIGER_STATIC) {
+        consider(static_plan());
+    } else if (knobs) {
+        eiger_plan_t p = *knobs;
+        if (variant != EIGER_AUTO) p.variant = variant;
+        if (dtype == EIGER_I32) p.narrow = 1;
+        consider(p);
+    } else {
+        const size_t l2 = l2_bytes_or_default();
+        for (int nok = 0; nok < 2; ++nok) {
+            eiger_plan_t p = plan_rules(variant, nb, np, dtype, nok != 0, l2);
+            if (dtype == EIGER_I32) p.narrow = 1;
+            consider(p);
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* eiger_last_error(void) { return g_last_error.c_str(); }
+
+const char* eiger_version(void) { return "eiger-gb300 0.1 (sm_103a)"; }
+
+eiger_status eiger_stats_workspace(int64_t n, eiger_dtype dtype, size_t* bytes) {
+    if (!bytes) return fail(EIGER_ERR_INVALID_ARG, "bytes is NULL");
+    if (n < 0) return fail(EIGER_ERR_INVALID_ARG, "n < 0");
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
+    Carve c{nullptr, 0};
+    stats_layout(c);
+    *bytes = c.off;
+    return EIGER_OK;
+}
+
+eiger_status eiger_stats(const void* d_keys, int64_t n, eiger_dtype dtype, eiger_stats_t* out,
+                         void* d_workspace, size_t ws_bytes, void* stream) {
+    if (!out) return fail(EIGER_ERR_INVALID_ARG, "out is NULL");
+    if (n < 0) return fail(EIGER_ERR_INVALID_ARG, "n < 0");
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
+    if (n > 0 && !d_keys) return fail(EIGER_ERR_INVALID_ARG, "NULL keys with n > 0");
+    if (d_keys && !aligned(d_keys, dtype == EIGER_I32 ? 4 : 8))
+        return fail(EIGER_ERR_INVALID_ARG, "keys must be aligned to their element size");
+    prof_reset();
+    Carve c{static_cast<char*>(d_workspace), 0};
+    StatsScratch ss = stats_layout(c);
+    if (n > 0 && (c.off > ws_bytes || !d_workspace))
+        return fail(EIGER_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, c.off);
+    return run_stats(d_keys, n, dtype, ss, static_cast<cudaStream_t>(stream), out);
+}
+
+eiger_status eiger_plan(const eiger_stats_t* build, const eiger_stats_t* probe, int64_t nb, int64_t np,
+                        eiger_dtype dtype, eiger_plan_t* out) {
+    (void)probe;
+    if (!out || !build) return fail(EIGER_ERR_INVALID_ARG, "NULL build statistics or output");
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
+    if (nb < 0 || np < 0 || nb > kMaxRows || np > kMaxRows)
+        return fail(EIGER_ERR_INVALID_ARG, "row counts must be in [0, 2^32)");
+    const bool nok = narrowable(dtype, nb, build->min, build->max);
+    *out = plan_rules(EIGER_AUTO, nb, np, dtype, nok, l2_bytes_or_default());
+    if (dtype == EIGER_I32) out->narrow = 1;
+    out->key_min = build->min;
+    out->key_max = build->max;
+    return EIGER_OK;
+}
+
+eiger_status eiger_join_workspace(int64_t nb, int64_t np, eiger_dtype dtype, eiger_variant variant,
+                                  const eiger_plan_t* knobs, size_t* bytes) {
+    if (!bytes) return fail(EIGER_ERR_INVALID_ARG, "bytes is NULL");
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
+    if (nb < 0 || np < 0 || nb > kMaxRows || np > kMaxRows)
+        return fail(EIGER_ERR_INVALID_ARG, "row counts must be in [0, 2^32)");
+    if (variant < EIGER_AUTO || variant > EIGER_STATIC) return fail(EIGER_ERR_INVALID_ARG, "bad variant");
+    *bytes = join_workspace_bytes(nb, np, dtype, variant, knobs);
+    return EIGER_OK;
+}
+
+eiger_status eiger_join(eiger_dtype dtype, const void* d_bkeys, const void* d_bpay, int64_t nb,
+                        const void* d_pkeys, const void* d_ppay, int64_t np, int32_t payload_bytes,
+                        eiger_variant variant, const eiger_plan_t* knobs, uint32_t* d_out_bidx,
+                        uint32_t* d_out_pidx, void* d_out_bpay, void* d_out_ppay, int64_t capacity,
+                        int64_t* out_count, void* d_workspace, size_t ws_bytes, eiger_plan_t* plan_used,
+                        void* stream) {
+    if (capacity < 0) return fail(EIGER_ERR_INVALID_ARG, "capacity < 0");
+    if (capacity > 0 && !d_out_bidx && !d_out_pidx && !d_out_bpay && !d_out_ppay)
+        return fail(EIGER_ERR_INVALID_ARG, "capacity > 0 but no output array");
+    JoinCall c{};
+    c.dtype = dtype;
+    c.bkeys = d_bkeys;
+    c.bpay = d_bpay;
+    c.nb = nb;
+    c.pkeys = d_pkeys;
+    c.ppay = d_ppay;
+    c.np = np;
+    c.pay_bytes = payload_bytes;
+    c.variant = variant;
+    c.knobs = knobs;
+    c.out.bidx = d_out_bidx;
+    c.out.pidx = d_out_pidx;
+    c.out.bpay_out = d_out_bpay;
+    c.out.ppay_out = d_out_ppay;
+    c.out.bpay = d_bpay;
+    c.out.ppay = d_ppay;
+    c.out.pay_bytes = payload_bytes;
+    c.out.aggregate = 0;
+    c.out.capacity = (unsigned long long)capacity;
+    c.out_count = out_count;
+    c.out_sum = nullptr;
+    c.ws = d_workspace;
+    c.ws_bytes = ws_bytes;
+    c.plan_used = plan_used;
+    c.stream = static_cast<cudaStream_t>(stream);
+    return run_join(c);
+}
+
+eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* d_bpay, int64_t nb,
+                            const void* d_pkeys, const void* d_ppay, int64_t np, int32_t payload_bytes,
+                            eiger_variant variant, const eiger_plan_t* knobs, int64_t* out_sum,
+                            int64_t* out_count, void* d_workspace, size_t ws_bytes,
+                            eiger_plan_t* plan_used, void* stream) {
+    if (!out_sum) return fail(EIGER_ERR_INVALID_ARG, "out_sum is NULL");
+    if ((nb > 0 && !d_bpay) || (np > 0 && !d_ppay))
+        return fail(EIGER_ERR_INVALID_ARG, "eiger_join_sum needs both payload columns");
+    JoinCall c{};
+    c.dtype = dtype;
+    c.bkeys = d_bkeys;
+    c.bpay = d_bpay;
+    c.nb = nb;
+    c.pkeys = d_pkeys;
+    c.ppay = d_ppay;
+    c.np = np;
+    c.pay_bytes = payload_bytes;
+    c.variant = variant;
+    c.knobs = knobs;
+    c.out.bpay = d_bpay;
+    c.out.ppay = d_ppay;
+    c.out.pay_bytes = payload_bytes;
+    c.out.aggregate = 1;
+    c.out.capacity = 0;
+    c.out_count = out_count;
+    c.out_sum = out_sum;
+    c.ws = d_workspace;
+    c.ws_bytes = ws_bytes;
+    c.plan_used = plan_used;
+    c.stream = static_cast<cudaStream_t>(stream);
+    return run_join(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// Internal definitions shared by the CUDA translation units of libeiger.
+// Nothing here is part of the public ABI (see include/eiger.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace eiger {
+
+// ---------------------------------------------------------------- constants
+
+constexpr int kHllP = 14;              // HyperLogLog precision p (Sec. 4.1)
+constexpr int kHllM = 1 << kHllP;      // m = 2^p registers
+constexpr int kRhoMax = 64 - kHllP + 1;  // rank when the 50 low hash bits are zero
+
+constexpr unsigned long long kEmptySlot = ~0ull;  // empty hash-table slot / idx word
+
+// Device-side error flags, OR-ed into Ctrl::err and mapped to statuses on the host.
+constexpr unsigned kErrTableFull = 1u;  // a probe sequence walked the whole table
+constexpr unsigned kErrInternal = 2u;   // a consistency check failed
+
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------- hashes
+
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014): the 64-bit
+// hash of the HyperLogLog sketch. Applied to the key's 64-bit two's-complement
+// pattern, so int32 keys are sign-extended first.
+__host__ __device__ __forceinline__ uint64_t sketch_hash(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// MurmurHash3 finalisers (Appleby): bijective avalanche mixers used to place
+// keys in hash tables and radix partitions. Partitions take the top bits of the
+// mixed key, table slots the low bits, so the two never overlap.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xFF51AFD7ED558CCDull;
+    k ^= k >> 33;
+    k *= 0xC4CEB9FE1A85EC53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// Key encodings carried through the join.
+//  - 32-bit: key' = (uint32)(key - offset). offset = build minimum when the
+//    build span fits 32 bits (range-offset narrowing, Sec. 4.3 frame of
+//    reference), or 0 for raw int32 keys (their bit pattern).
+//  - 64-bit: key' = the int64 bit pattern.
+template <typename KeyT>
+struct KeyCodec;
+
+template <>
+struct KeyCodec<uint32_t> {
+    static constexpr int kBits = 32;
+    __device__ __forceinline__ static uint32_t encode(int64_t k, uint64_t offset) {
+        return (uint32_t)((uint64_t)k - offset);
+    }
+    __device__ __forceinline__ static uint32_t hash(uint32_t k) { return mix32(k); }
+};
+
+template <>
+struct KeyCodec<uint64_t> {
+    static constexpr int kBits = 64;
+    __device__ __forceinline__ static uint64_t encode(int64_t k, uint64_t) { return (uint64_t)k; }
+    __device__ __forceinline__ static uint64_t hash(uint64_t k) { return mix64(k); }
+};
+
+// Probe-side range test: a key outside [lo, hi] of the build side cannot match.
+struct KeyRange {
+    int64_t lo, hi;
+    uint64_t offset;  // encoding offset (see KeyCodec)
+};
+
+// ---------------------------------------------------------------- control
+
+// Small control block at the start of every join workspace.
+struct Ctrl {
+    unsigned long long cursor;     // matches found (output cursor)
+    unsigned long long sum;        // aggregate mode: sum of payload pairs mod 2^64
+    unsigned long long next_item;  // PHJ work-item dispenser
+    unsigned long long nitems;     // PHJ work items
+    unsigned int err;              // kErr* flags
+    unsigned int ntiles2[2];       // pass-2 tile count per side (build, probe)
+    unsigned int kept[2];          // rows kept by the range test per side
+    unsigned int pad[3];
+};
+
+// Output of one join: materialised arrays or a fused aggregate.
+struct JoinOut {
+    uint32_t* bidx;
+    uint32_t* pidx;
+    void* bpay_out;
+    void* ppay_out;
+    const void* bpay;  // payload columns gathered by tuple ID (GFUR)
+    const void* ppay;
+    int pay_bytes;
+    int aggregate;  // 1: accumulate sum/count only
+    unsigned long long capacity;
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & (kWarp - 1); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int64_t read_pay(const void* p, int bytes, uint32_t i) {
+    return bytes == 4 ? (int64_t)((const int32_t*)p)[i] : ((const int64_t*)p)[i];
+}
+
+__device__ __forceinline__ void write_pay(void* p, int bytes, unsigned long long i, int64_t v) {
+    if (bytes == 4)
+        ((int32_t*)p)[i] = (int32_t)v;
+    else
+        ((int64_t*)p)[i] = v;
+}
+
+__host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) {
+    return (x + a - 1) / a * a;
+}
+
+// Bump allocator over a caller-provided workspace; with base == nullptr it only
+// measures, so one layout function serves both the size query and the carving.
+struct Carve {
+    char* base;
+    size_t off;
+    template <typename T>
+    T* take(size_t count) {
+        off = align_up(off, 256);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+inline int ceil_log2_u64(unsigned long long x) {
+    int b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+// ---------------------------------------------------------------- device info
+
+struct DevInfo {
+    int dev;
+    int sms;
+    int smem_optin;   // max dynamic shared memory per block (opt-in)
+    int l2_bytes;
+    int max_threads_sm;
+};
+
+// Cached properties of the current device; returns cudaSuccess or the error.
+cudaError_t current_device_info(DevInfo* out);
+
+}  // namespace eiger

@@ -1,0 +1,114 @@
+// Match emission shared by the join kernels.
+//
+// Matches are staged per CTA in shared memory: a warp reserves room for all of
+// its matching lanes with one shared-memory atomic (ballot + popc), and the CTA
+// reserves room in the global output with one global atomic per flush. That
+// keeps the output writes coalesced and the single global cursor cold (one
+// atomic per ~thousand matches instead of one per warp). If a CTA produces more
+// matches between two flushes than the stage holds (duplicate-heavy keys), the
+// lanes that do not fit write straight to global memory with a warp-aggregated
+// atomic, so no match is ever lost and no stage size bounds the multiplicity.
+//
+// In aggregate mode nothing is written: each thread accumulates the payload
+// sum and the match count, reduced once per CTA at the end.
+#pragma once
+
+#include "common.cuh"
+
+namespace eiger {
+
+template <int STAGE>
+struct Stage {
+    uint32_t b[STAGE];
+    uint32_t p[STAGE];
+    unsigned int count;
+    unsigned long long base;
+};
+
+__device__ __forceinline__ void write_match(const JoinOut& out, unsigned long long pos, uint32_t b,
+                                            uint32_t p) {
+    if (pos >= out.capacity) return;
+    if (out.bidx) out.bidx[pos] = b;
+    if (out.pidx) out.pidx[pos] = p;
+    if (out.bpay_out) write_pay(out.bpay_out, out.pay_bytes, pos, read_pay(out.bpay, out.pay_bytes, b));
+    if (out.ppay_out) write_pay(out.ppay_out, out.pay_bytes, pos, read_pay(out.ppay, out.pay_bytes, p));
+}
+
+struct AggState {
+    unsigned long long sum;
+    unsigned long long count;
+};
+
+// Warp-collective: all 32 lanes call it; lanes with `has` emit the pair (b, p).
+template <bool AGG, int STAGE>
+__device__ __forceinline__ void emit(Stage<STAGE>& st, AggState& agg, bool has, uint32_t b,
+                                     uint32_t p, const JoinOut& out, Ctrl* ctrl) {
+    if (AGG) {
+        if (has) {
+            agg.sum += (unsigned long long)read_pay(out.bpay, out.pay_bytes, b) +
+                       (unsigned long long)read_pay(out.ppay, out.pay_bytes, p);
+            agg.count += 1;
+        }
+        return;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, has);
+    if (mask == 0) return;
+    const unsigned lane = lane_id();
+    const int leader = __ffs(mask) - 1;
+    unsigned pos0 = 0;
+    if ((int)lane == leader) pos0 = atomicAdd(&st.count, (unsigned)__popc(mask));
+    pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+    const unsigned pos = pos0 + __popc(mask & lanemask_lt());
+    const bool spill = has && pos >= (unsigned)STAGE;
+    if (has && !spill) {
+        st.b[pos] = b;
+        st.p[pos] = p;
+    }
+    const unsigned smask = __ballot_sync(0xffffffffu, spill);
+    if (smask) {
+        const int sl = __ffs(smask) - 1;
+        unsigned long long g0 = 0;
+        if ((int)lane == sl) g0 = atomicAdd(&ctrl->cursor, (unsigned long long)__popc(smask));
+        g0 = __shfl_sync(0xffffffffu, g0, sl);
+        if (spill) write_match(out, g0 + __popc(smask & lanemask_lt()), b, p);
+    }
+}
+
+// Block-collective: writes the staged matches out and empties the stage.
+template <bool AGG, int STAGE>
+__device__ __forceinline__ void stage_flush(Stage<STAGE>& st, const JoinOut& out, Ctrl* ctrl) {
+    if (AGG) return;
+    __syncthreads();
+    const unsigned n = st.count < (unsigned)STAGE ? st.count : (unsigned)STAGE;
+    if (threadIdx.x == 0) st.base = n ? atomicAdd(&ctrl->cursor, (unsigned long long)n) : 0ull;
+    __syncthreads();
+    const unsigned long long base = st.base;
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) write_match(out, base + i, st.b[i], st.p[i]);
+    __syncthreads();
+    if (threadIdx.x == 0) st.count = 0;
+    __syncthreads();
+}
+
+// Block-collective: true when the stage may not hold another `room` matches.
+// The first barrier orders every emit before the read; the second keeps the
+// count unchanged until thread 0 has read it.
+template <int STAGE>
+__device__ __forceinline__ bool stage_nearly_full(Stage<STAGE>& st, unsigned room) {
+    __syncthreads();
+    return __syncthreads_or(threadIdx.x == 0 && st.count + room > (unsigned)STAGE) != 0;
+}
+
+// Once per thread at kernel end (aggregate mode): warp-reduce, one atomic pair.
+__device__ __forceinline__ void agg_commit(AggState& agg, Ctrl* ctrl) {
+#pragma unroll
+    for (int o = kWarp / 2; o > 0; o >>= 1) {
+        agg.sum += __shfl_xor_sync(0xffffffffu, agg.sum, o);
+        agg.count += __shfl_xor_sync(0xffffffffu, agg.count, o);
+    }
+    if (lane_id() == 0 && agg.count) {
+        atomicAdd(&ctrl->sum, agg.sum);
+        atomicAdd(&ctrl->cursor, agg.count);
+    }
+}
+
+}  // namespace eiger

@@ -1,0 +1,546 @@
+// Radix partitioning for the partitioned hash join (Sec. 3.2, the PHJ the
+// paper adopts; partitions are taken on bits of a hash of the key so their
+// sizes are even, as Sec. 3.3 does before partitioning).
+//
+// Each pass splits every input segment by `bits` further bits of mix(key'):
+// pass 1 by the top b1 bits, pass 2 by the next b2 bits within each pass-1
+// partition. A pass runs three steps over fixed tiles of kPartTile rows:
+//   hist    per tile, a shared-memory histogram of the digits, written to a
+//           counts array laid out [segment][digit][tile-in-segment];
+//   scan    one device-wide exclusive scan of that array, which turns every
+//           (tile, digit) count into the global output offset of that tile's
+//           run of the digit (segments stay contiguous and in order);
+//   scatter per tile, rank each row within its digit with a shared-memory
+//           atomic, stage the tile in shared memory grouped by digit, then
+//           write each digit run to its global offset with consecutive
+//           threads on consecutive addresses (coalesced runs instead of one
+//           scattered 8-byte store per row).
+// The first pass reads the raw key column (row ids are implicit), applies the
+// probe-side range test (a probe key outside [min_R, max_R] cannot match and
+// is dropped here) and the frame-of-reference narrowing; later passes read the
+// (key', row) pairs of the previous pass.
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace eiger {
+
+namespace {
+
+constexpr int kPartThreads = 256;
+constexpr int kPartItems = kPartTile / kPartThreads;  // 16 rows per thread
+constexpr uint32_t kNoDigit = 0xFFFFFFFFu;
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+template <typename InKey, typename KeyT>
+struct PartPass {
+    const InKey* raw;        // pass 1 input: raw key column
+    const KeyT* in_key;      // later passes: previous pass output
+    const uint32_t* in_idx;
+    KeyT* out_key;
+    uint32_t* out_idx;
+    uint32_t n;              // pass 1: rows
+    KeyRange rng;
+    int check_range;
+    int dshift;              // digit = (hash >> dshift) & dmask
+    uint32_t dmask;
+    int bits;
+    uint32_t* counts;
+    const Tile* tiles;       // nullptr: pass-1 tiling of [0, n)
+    const uint32_t* ntiles_dev;
+    uint32_t ntiles_fixed;
+};
+
+template <typename InKey, typename KeyT>
+__device__ __forceinline__ Tile get_tile(const PartPass<InKey, KeyT>& a, uint32_t t) {
+    if (a.tiles) return a.tiles[t];
+    Tile tl;
+    tl.start = t * (uint32_t)kPartTile;
+    const uint32_t rest = a.n - tl.start;
+    tl.len = rest < (uint32_t)kPartTile ? rest : (uint32_t)kPartTile;
+    tl.seg = 0;
+    tl.tile_base = 0;
+    tl.ntiles_seg = a.ntiles_fixed;
+    return tl;
+}
+
+__device__ __forceinline__ size_t count_index(const Tile& tl, uint32_t t, uint32_t d, int bits) {
+    return ((size_t)tl.tile_base << bits) + (size_t)d * tl.ntiles_seg + (t - tl.tile_base);
+}
+
+template <typename InKey, typename KeyT, bool FIRST>
+__device__ __forceinline__ bool part_load(const PartPass<InKey, KeyT>& a, uint32_t r, KeyT& k,
+                                          uint32_t& id) {
+    if (FIRST) {
+        const int64_t key = (int64_t)__ldcs(a.raw + r);
+        if (a.check_range && (key < a.rng.lo || key > a.rng.hi)) return false;
+        k = KeyCodec<KeyT>::encode(key, a.rng.offset);
+        id = r;
+    } else {
+        k = __ldcs(a.in_key + r);
+        id = __ldcs(a.in_idx + r);
+    }
+    return true;
+}
+
+template <typename KeyT>
+__device__ __forceinline__ uint32_t digit_of(KeyT k, int dshift, uint32_t dmask) {
+    return (uint32_t)(KeyCodec<KeyT>::hash(k) >> dshift) & dmask;
+}
+
+// Exclusive scan of in[0, n) into out[0, n), n <= kPartItems * blockDim.x.
+// Block-collective; returns the total. s_warp: blockDim.x / 32 words.
+__device__ uint32_t block_scan_smem(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* s_warp) {
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    uint32_t beg = threadIdx.x * per;
+    if (beg > n) beg = n;
+    uint32_t end = beg + per;
+    if (end > n) end = n;
+    uint32_t local = 0;
+    for (uint32_t i = beg; i < end; ++i) local += in[i];
+    uint32_t x = local;
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane >= o) x += y;
+    }
+    const int warp = threadIdx.x / kWarp;
+    const int nw = blockDim.x / kWarp;
+    __syncthreads();
+    if ((int)lane == kWarp - 1) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = (int)lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if ((int)lane >= o) v += y;
+        }
+        if ((int)lane < nw) s_warp[lane] = v;
+    }
+    __syncthreads();
+    uint32_t prefix = (warp ? s_warp[warp - 1] : 0u) + x - local;
+    const uint32_t total = s_warp[nw - 1];
+    for (uint32_t i = beg; i < end; ++i) {
+        out[i] = prefix;
+        prefix += in[i];
+    }
+    return total;
+}
+
+template <typename InKey, typename KeyT, bool FIRST>
+__global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey, KeyT> a) {
+    extern __shared__ uint32_t s_cnt[];
+    const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
+    const uint32_t nd = 1u << a.bits;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile tl = get_tile(a, t);
+        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
+        __syncthreads();
+        KeyT kk[kPartItems];
+        bool ok[kPartItems];
+#pragma unroll
+        for (int j = 0; j < kPartItems; ++j) {
+            const uint32_t e = j * kPartThreads + threadIdx.x;
+            uint32_t id;
+            ok[j] = e < tl.len && part_load<InKey, KeyT, FIRST>(a, tl.start + e, kk[j], id);
+        }
+#pragma unroll
+        for (int j = 0; j < kPartItems; ++j)
+            if (ok[j]) atomicAdd(&s_cnt[digit_of(kk[j], a.dshift, a.dmask)], 1u);
+        __syncthreads();
+        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x)
+            a.counts[count_index(tl, t, d, a.bits)] = s_cnt[d];
+        __syncthreads();
+    }
+}
+
+template <typename KeyT>
+__host__ __device__ constexpr size_t scatter_smem_bytes(int bits) {
+    return align_up(3 * ((size_t)1 << bits) * sizeof(uint32_t), 16) +
+           (size_t)kPartTile * (sizeof(KeyT) + sizeof(uint32_t));
+}
+
+template <typename InKey, typename KeyT, bool FIRST>
+__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InKey, KeyT> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_warp[kPartThreads / kWarp];
+    __shared__ uint32_t s_kept;
+    const uint32_t nd = 1u << a.bits;
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* s_start = s_cnt + nd;
+    uint32_t* s_goff = s_start + nd;
+    KeyT* s_key = reinterpret_cast<KeyT*>(smem + align_up(3 * (size_t)nd * sizeof(uint32_t), 16));
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_key + kPartTile);
+
+    const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile tl = get_tile(a, t);
+        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
+        __syncthreads();
+
+        KeyT kk[kPartItems];
+        uint32_t ii[kPartItems];
+        uint32_t dr[kPartItems];  // (rank << 12) | digit, or kNoDigit
+#pragma unroll
+        for (int j = 0; j < kPartItems; ++j) {
+            const uint32_t e = j * kPartThreads + threadIdx.x;
+            dr[j] = kNoDigit;
+            if (e < tl.len && part_load<InKey, KeyT, FIRST>(a, tl.start + e, kk[j], ii[j]))
+                dr[j] = digit_of(kk[j], a.dshift, a.dmask);
+        }
+#pragma unroll
+        for (int j = 0; j < kPartItems; ++j)
+            if (dr[j] != kNoDigit) dr[j] |= atomicAdd(&s_cnt[dr[j]], 1u) << 12;
+        __syncthreads();
+
+        const uint32_t kept = block_scan_smem(s_cnt, s_start, nd, s_warp);
+        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x)
+            s_goff[d] = s_cnt[d] ? a.counts[count_index(tl, t, d, a.bits)] : 0u;
+        if (threadIdx.x == 0) s_kept = kept;
+        __syncthreads();
+
+#pragma unroll
+        for (int j = 0; j < kPartItems; ++j) {
+            if (dr[j] != kNoDigit) {
+                const uint32_t pos = s_start[dr[j] & 0xFFFu] + (dr[j] >> 12);
+                s_key[pos] = kk[j];
+                s_idx[pos] = ii[j];
+            }
+        }
+        __syncthreads();
+
+        const uint32_t nk = s_kept;
+        for (uint32_t pos = threadIdx.x; pos < nk; pos += blockDim.x) {
+            const KeyT k = s_key[pos];
+            const uint32_t d = digit_of(k, a.dshift, a.dmask);
+            const uint32_t g = s_goff[d] + (pos - s_start[d]);
+            a.out_key[g] = k;
+            a.out_idx[g] = s_idx[pos];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ device-wide scan
+
+struct ScanLen {
+    size_t fixed;
+    const uint32_t* ntiles_dev;  // when set: length = *ntiles_dev << bits
+    int bits;
+    __device__ __forceinline__ size_t get() const {
+        return ntiles_dev ? ((size_t)*ntiles_dev << bits) : fixed;
+    }
+};
+
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* s_warp) {
+#pragma unroll
+    for (int o = kWarp / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane_id() == 0) s_warp[threadIdx.x / kWarp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x / kWarp); ++w) t += s_warp[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    scan_reduce_kernel(const uint32_t* __restrict__ data, ScanLen L, uint32_t* __restrict__ block_sums) {
+    __shared__ uint32_t s_warp[kScanThreads / kWarp];
+    const size_t len = L.get();
+    const size_t beg = (size_t)blockIdx.x * kScanChunk;
+    uint32_t v = 0;
+    for (size_t i = beg + threadIdx.x; i < beg + kScanChunk && i < len; i += blockDim.x) v += data[i];
+    v = block_sum(v, s_warp);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = v;
+}
+
+// One block: exclusive scan of block_sums[0, nblocks) in place; *total = sum.
+__global__ void __launch_bounds__(1024)
+    scan_blocksums_kernel(uint32_t* __restrict__ block_sums, uint32_t nblocks, uint32_t* total) {
+    __shared__ uint32_t s_in[1024];
+    __shared__ uint32_t s_out[1024];
+    __shared__ uint32_t s_warp[1024 / kWarp];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nblocks; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        s_in[threadIdx.x] = i < nblocks ? block_sums[i] : 0u;
+        __syncthreads();
+        const uint32_t m = nblocks - base < 1024u ? nblocks - base : 1024u;
+        const uint32_t t = block_scan_smem(s_in, s_out, m, s_warp);
+        __syncthreads();
+        if (i < nblocks) block_sums[i] = s_out[threadIdx.x] + carry;
+        carry += t;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    scan_apply_kernel(uint32_t* __restrict__ data, ScanLen L, const uint32_t* __restrict__ block_sums) {
+    __shared__ uint32_t s_buf[kScanChunk];
+    __shared__ uint32_t s_warp[kScanThreads / kWarp];
+    const size_t len = L.get();
+    const size_t beg = (size_t)blockIdx.x * kScanChunk;
+    if (beg >= len) return;
+    const uint32_t m = (uint32_t)(len - beg < (size_t)kScanChunk ? len - beg : (size_t)kScanChunk);
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) s_buf[i] = data[beg + i];
+    __syncthreads();
+    // per-thread run of kScanItems consecutive entries
+    const uint32_t lo = threadIdx.x * kScanItems;
+    uint32_t local = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (lo + j < m) local += s_buf[lo + j];
+    uint32_t x = local;
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane >= o) x += y;
+    }
+    const int warp = threadIdx.x / kWarp;
+    if ((int)lane == kWarp - 1) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = s_warp[lane < kScanThreads / kWarp ? lane : 0];
+        if (lane >= kScanThreads / kWarp) v = 0;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if ((int)lane >= o) v += y;
+        }
+        if (lane < kScanThreads / kWarp) s_warp[lane] = v;
+    }
+    __syncthreads();
+    uint32_t prefix = block_sums[blockIdx.x] + (warp ? s_warp[warp - 1] : 0u) + x - local;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (lo + j < m) {
+            const uint32_t v = s_buf[lo + j];
+            s_buf[lo + j] = prefix;
+            prefix += v;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) data[beg + i] = s_buf[i];
+}
+
+// ------------------------------------------------------------ pass-2 tiling
+
+// One block. From the scanned pass-1 counts, the pass-1 partitions become the
+// pass-2 segments; each is cut into tiles of kPartTile rows.
+__global__ void __launch_bounds__(1024)
+    seg_tiles_kernel(const uint32_t* __restrict__ counts1, uint32_t ntiles1, int b1,
+                     const uint32_t* __restrict__ total1, SegInfo* __restrict__ segs,
+                     Tile* __restrict__ tiles, uint32_t* __restrict__ ntiles2) {
+    __shared__ uint32_t s_nt[1u << kMaxBits];
+    __shared__ uint32_t s_base[1u << kMaxBits];
+    __shared__ uint32_t s_warp[1024 / kWarp];
+    const uint32_t nseg = 1u << b1;
+    for (uint32_t s = threadIdx.x; s < nseg; s += blockDim.x) {
+        const uint32_t st = ntiles1 ? counts1[(size_t)s * ntiles1] : 0u;
+        const uint32_t en = s + 1 < nseg ? (ntiles1 ? counts1[(size_t)(s + 1) * ntiles1] : 0u) : *total1;
+        const uint32_t sz = en - st;
+        segs[s].start = st;
+        segs[s].size = sz;
+        s_nt[s] = (sz + kPartTile - 1) / kPartTile;
+    }
+    __syncthreads();
+    const uint32_t total = block_scan_smem(s_nt, s_base, nseg, s_warp);
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < nseg; s += blockDim.x) {
+        const uint32_t nt = s_nt[s], base = s_base[s];
+        segs[s].tile_base = base;
+        segs[s].ntiles = nt;
+        const uint32_t st = segs[s].start, sz = segs[s].size;
+        for (uint32_t k = 0; k < nt; ++k) {
+            Tile tl;
+            tl.start = st + k * kPartTile;
+            const uint32_t rest = sz - k * kPartTile;
+            tl.len = rest < (uint32_t)kPartTile ? rest : (uint32_t)kPartTile;
+            tl.seg = s;
+            tl.tile_base = base;
+            tl.ntiles_seg = nt;
+            tiles[base + k] = tl;
+        }
+    }
+    if (threadIdx.x == 0) *ntiles2 = total;
+}
+
+// Start of every final partition, plus part_start[P] = rows kept.
+__global__ void part_start_kernel(const uint32_t* __restrict__ counts, int passes, uint32_t ntiles1,
+                                  int b1, int b2, const SegInfo* __restrict__ segs,
+                                  const uint32_t* __restrict__ total, uint32_t* __restrict__ part_start) {
+    const uint32_t P = 1u << (b1 + b2);
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p <= P; p += gridDim.x * blockDim.x) {
+        uint32_t v;
+        if (p == P) {
+            v = *total;
+        } else if (passes == 1) {
+            v = ntiles1 ? counts[(size_t)p * ntiles1] : 0u;
+        } else {
+            const SegInfo sg = segs[p >> b2];
+            const uint32_t d2 = p & ((1u << b2) - 1u);
+            v = sg.ntiles ? counts[((size_t)sg.tile_base << b2) + (size_t)d2 * sg.ntiles] : sg.start;
+        }
+        part_start[p] = v;
+    }
+}
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename K>
+int occupancy_grid(K kern, int threads, size_t smem, const DevInfo& di, size_t work) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    size_t g = (size_t)di.sms * per_sm;
+    if (work < g) g = work;
+    return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t scan_counts(uint32_t* counts, ScanLen L, size_t max_len, uint32_t* block_sums,
+                        uint32_t* total, cudaStream_t stream) {
+    const uint32_t nblocks = (uint32_t)((max_len + kScanChunk - 1) / kScanChunk);
+    const uint32_t g = nblocks ? nblocks : 1;
+    scan_reduce_kernel<<<g, kScanThreads, 0, stream>>>(counts, L, block_sums);
+    scan_blocksums_kernel<<<1, 1024, 0, stream>>>(block_sums, g, total);
+    scan_apply_kernel<<<g, kScanThreads, 0, stream>>>(counts, L, block_sums);
+    return cudaGetLastError();
+}
+
+// One partitioning pass over n rows. Algorithmic bytes per launch: the
+// histogram reads each key once; the scatter reads each (key, row) once and
+// writes each kept (key', row) once; the scan reads and writes the counts.
+template <typename InKey, typename KeyT>
+cudaError_t run_pass(PartPass<InKey, KeyT> a, bool first, size_t max_tiles, const PartSide& s,
+                     uint32_t* total, const DevInfo& di, cudaStream_t stream, const char* side_name) {
+    cudaError_t e;
+    const size_t hsmem = ((size_t)1 << a.bits) * sizeof(uint32_t);
+    const size_t ssmem = scatter_smem_bytes<KeyT>(a.bits);
+    auto hist = first ? part_hist_kernel<InKey, KeyT, true> : part_hist_kernel<InKey, KeyT, false>;
+    auto scat = first ? part_scatter_kernel<InKey, KeyT, true> : part_scatter_kernel<InKey, KeyT, false>;
+    if ((e = set_smem(hist, hsmem)) != cudaSuccess) return e;
+    if ((e = set_smem(scat, ssmem)) != cudaSuccess) return e;
+    const double n = (double)a.n;
+    const double in_key = first ? (double)sizeof(InKey) : (double)sizeof(KeyT);
+    const double tuple = (double)(sizeof(KeyT) + sizeof(uint32_t));
+    const double in_tuple = first ? (double)sizeof(InKey) : tuple;
+    char name[32];
+    {
+        snprintf(name, sizeof name, "part_hist.%s.%s", first ? "p1" : "p2", side_name);
+        ProfScope ps(name, n * in_key, stream);
+        hist<<<occupancy_grid(hist, kPartThreads, hsmem, di, max_tiles), kPartThreads, hsmem, stream>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    ScanLen L{max_tiles << a.bits, a.tiles ? a.ntiles_dev : nullptr, a.bits};
+    {
+        snprintf(name, sizeof name, "part_scan.%s.%s", first ? "p1" : "p2", side_name);
+        ProfScope ps(name, 12.0 * (double)(max_tiles << a.bits), stream, 0.0, 3);
+        if ((e = scan_counts(a.counts, L, max_tiles << a.bits, s.block_sums, total, stream)) != cudaSuccess)
+            return e;
+    }
+    snprintf(name, sizeof name, "part_scatter.%s.%s", first ? "p1" : "p2", side_name);
+    ProfScope ps(name, n * (in_tuple + tuple), stream);
+    scat<<<occupancy_grid(scat, kPartThreads, ssmem, di, max_tiles), kPartThreads, ssmem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename InKey, typename KeyT>
+cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanDev& plan,
+                            const PartSide& s, const DevInfo& di, cudaStream_t stream) {
+    const int passes = plan.variant == 3 ? 2 : 1;
+    const int b1 = plan.bits1, b2 = passes == 2 ? plan.bits2 : 0;
+    const uint32_t ntiles1 = (n + kPartTile - 1) / kPartTile;
+    cudaError_t e;
+
+    PartPass<InKey, KeyT> a{};
+    a.raw = keys;
+    a.out_key = static_cast<KeyT*>(s.key[0]);
+    a.out_idx = s.idx[0];
+    a.n = n;
+    a.rng = plan.range;
+    a.check_range = side == 1 ? plan.check_range : 0;
+    a.dshift = KeyCodec<KeyT>::kBits - b1;
+    a.dmask = (1u << b1) - 1u;
+    a.bits = b1;
+    a.counts = s.counts;
+    a.tiles = nullptr;
+    a.ntiles_fixed = ntiles1;
+    const char* sn = side == 0 ? "build" : "probe";
+    if ((e = run_pass(a, true, ntiles1, s, s.total, di, stream, sn)) != cudaSuccess) return e;
+
+    if (passes == 2) {
+        ProfScope ps("seg_tiles", 0.0, stream);
+        seg_tiles_kernel<<<1, 1024, 0, stream>>>(s.counts, ntiles1, b1, s.total, s.segs, s.tiles,
+                                                 s.total + 2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        PartPass<InKey, KeyT> b{};
+        b.in_key = static_cast<const KeyT*>(s.key[0]);
+        b.in_idx = s.idx[0];
+        b.out_key = static_cast<KeyT*>(s.key[1]);
+        b.out_idx = s.idx[1];
+        b.n = n;
+        b.rng = plan.range;
+        b.check_range = 0;
+        b.dshift = KeyCodec<KeyT>::kBits - b1 - b2;
+        b.dmask = (1u << b2) - 1u;
+        b.bits = b2;
+        b.counts = s.counts;
+        b.tiles = s.tiles;
+        b.ntiles_dev = s.total + 2;
+        const size_t max_tiles2 = (size_t)ntiles1 + ((size_t)1 << b1);
+        if ((e = run_pass(b, false, max_tiles2, s, s.total + 1, di, stream, sn)) != cudaSuccess) return e;
+    }
+    const uint32_t P = 1u << (b1 + b2);
+    const int threads = 256;
+    const int blocks = (int)((P + 1 + threads - 1) / threads);
+    ProfScope ps("part_start", 8.0 * (P + 1), stream);
+    part_start_kernel<<<blocks, threads, 0, stream>>>(s.counts, passes, ntiles1, b1, b2, s.segs, s.total,
+                                                      s.part_start);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t part_counts_len(int64_t n, int b1, int b2, int passes) {
+    const size_t ntiles1 = (size_t)((n + kPartTile - 1) / kPartTile);
+    size_t l1 = ntiles1 << b1;
+    size_t l2 = passes == 2 ? (ntiles1 + ((size_t)1 << b1)) << b2 : 0;
+    return l1 > l2 ? l1 : l2;
+}
+
+size_t part_scan_blocks(size_t counts_len) { return (counts_len + kScanChunk - 1) / kScanChunk + 1; }
+
+size_t part_scatter_smem(int bits, int key32) {
+    return key32 ? scatter_smem_bytes<uint32_t>(bits) : scatter_smem_bytes<uint64_t>(bits);
+}
+
+cudaError_t partition_side(const void* keys, int64_t n, int side, const PlanDev& plan,
+                           const PartSide& s, cudaStream_t stream) {
+    DevInfo di;
+    cudaError_t e = current_device_info(&di);
+    if (e != cudaSuccess) return e;
+    const uint32_t nn = (uint32_t)n;
+    if (plan.key32) {
+        if (plan.dtype == 0)
+            return partition_typed<int32_t, uint32_t>(static_cast<const int32_t*>(keys), nn, side, plan,
+                                                      s, di, stream);
+        return partition_typed<int64_t, uint32_t>(static_cast<const int64_t*>(keys), nn, side, plan, s,
+                                                  di, stream);
+    }
+    return partition_typed<int64_t, uint64_t>(static_cast<const int64_t*>(keys), nn, side, plan, s, di,
+                                              stream);
+}
+
+}  // namespace eiger

@@ -1,0 +1,96 @@
+// Rule-based variant selector and knob tuner (host only).
+//
+// The paper defers the join algorithm and its knobs to run time and decides
+// them from cheap statistics (Sec. 1 "algorithm selection" and "knob tuning";
+// Table 1: relation cardinalities, key distribution and data types decide the
+// join; Sec. 5.2.1-5.2.2: the non-partitioned hash join wins while its table
+// stays cache-resident, the partitioned join wins beyond). The rules below
+// encode that on a GB300:
+//  - keys are narrowed to 32 bits whenever the build range spans < 2^32
+//    (frame of reference, Sec. 4.3), which halves table slots and partition
+//    tuples;
+//  - NPHJ while its table (load factor 0.5) fits half of the L2 cache;
+//  - otherwise PHJ with enough radix bits that an average build partition
+//    holds about half a shared-memory table (kTargetRows), in one pass up to
+//    kOnePassBits bits and in two balanced passes beyond.
+#include <algorithm>
+#include <cmath>
+
+#include "planner.h"
+
+namespace eiger {
+
+namespace {
+constexpr int64_t kTargetRows = 2048;  // average build rows per partition
+constexpr int kOnePassBits = 8;
+constexpr int kMaxTotalBits = 20;
+}  // namespace
+
+int phj_total_bits(int64_t nb) {
+    const int64_t parts = (nb + kTargetRows - 1) / kTargetRows;
+    int b = 0;
+    while ((1ll << b) < parts) ++b;
+    if (b < 2) b = 2;
+    if (b > kMaxTotalBits) b = kMaxTotalBits;
+    return b;
+}
+
+unsigned long long table_slots(int64_t nb, double load_factor) {
+    const double want = (double)(nb > 0 ? nb : 1) / load_factor;
+    unsigned long long s = 64;
+    while ((double)s < want) s <<= 1;
+    return s;
+}
+
+eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool narrowable,
+                        size_t l2_bytes) {
+    (void)np;
+    eiger_plan_t p{};
+    p.selector = 0;
+    p.load_factor = 0.5f;
+    p.narrow = narrowable ? 1 : 0;
+    const bool key32 = dtype == EIGER_I32 || narrowable;
+    const int B = phj_total_bits(nb);
+    int v = variant;
+    if (v == EIGER_AUTO) {
+        const unsigned long long bytes = table_slots(nb, 0.5) * (key32 ? 8ull : 16ull);
+        if (bytes <= l2_bytes / 2)
+            v = EIGER_NPHJ;
+        else
+            v = B <= kOnePassBits ? EIGER_PHJ1 : EIGER_PHJ2;
+    }
+    p.variant = v;
+    if (v == EIGER_PHJ1) {
+        p.bits1 = std::min(B, 12);
+        p.bits2 = 0;
+    } else if (v == EIGER_PHJ2) {
+        p.bits1 = (B + 1) / 2;
+        p.bits2 = B - p.bits1;
+        if (p.bits2 < 1) {
+            p.bits1 = 1;
+            p.bits2 = 1;
+        }
+    }
+    return p;
+}
+
+// HyperLogLog estimate (Flajolet et al. 2007, with HyperLogLog++'s 64-bit hash:
+// no large-range correction) from the dense registers: the raw estimate
+// alpha_m m^2 / sum_j 2^-reg[j], replaced by linear counting m ln(m / V) when V
+// registers are still zero and the raw estimate is at most 2.5 m. The harmonic
+// sum is accumulated exactly as an integer count of 2^-kRhoMax units, so the
+// only rounding is the final fp64 expression, evaluated in a fixed order.
+double hll_estimate(const uint8_t* regs) {
+    constexpr int kRho = 64 - EIGER_HLL_P + 1;  // largest rank
+    uint32_t hist[kRho + 1] = {0};
+    for (int j = 0; j < EIGER_HLL_M; ++j) hist[regs[j] <= kRho ? regs[j] : kRho] += 1;
+    unsigned __int128 units = 0;
+    for (int r = 0; r <= kRho; ++r) units += (unsigned __int128)hist[r] << (kRho - r);
+    const double m = (double)EIGER_HLL_M;
+    const double alpha = 0.7213 / (1.0 + 1.079 / m);
+    double est = alpha * m * m * std::ldexp(1.0, kRho) / (double)units;
+    if (hist[0] != 0 && est <= 2.5 * m) est = m * std::log(m / (double)hist[0]);
+    return est;
+}
+
+}  // namespace eiger

@@ -1,0 +1,25 @@
+// Host-side planner interface (internal).
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "eiger.h"
+
+namespace eiger {
+
+// Radix bits the partitioned join uses for nb build rows.
+int phj_total_bits(int64_t nb);
+
+// Power-of-two slot count of a hash table holding nb rows at load_factor.
+unsigned long long table_slots(int64_t nb, double load_factor);
+
+// Plan for `variant` (EIGER_AUTO lets the rules choose) from sizes and
+// whether the build keys narrow to 32 bits.
+eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool narrowable,
+                        size_t l2_bytes);
+
+// HyperLogLog estimate from 2^14 dense registers (Sec. 4.1).
+double hll_estimate(const uint8_t* regs);
+
+}  // namespace eiger

@@ -1,0 +1,338 @@
+"""Python binding of libeiger's C ABI (``include/eiger.h``).
+
+Argument marshalling only: tensors become device pointers, the current torch
+stream becomes the ``stream`` argument, statuses become exceptions. Every step
+of the join runs in the library's CUDA kernels; if ``libeiger.so`` is missing
+or cannot be loaded, every call raises instead of computing anything here.
+
+PyTorch supplies device memory (inputs, outputs, workspace) and streams.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libeiger.so")
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_WORKSPACE, ERR_TABLE_FULL, ERR_CUDA, ERR_INTERNAL = range(7)
+I32, I64 = 0, 1
+AUTO, NPHJ, PHJ1, PHJ2, STATIC = range(5)
+VARIANTS = {"auto": AUTO, "nphj": NPHJ, "phj1": PHJ1, "phj2": PHJ2, "static": STATIC}
+VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
+HLL_M = 16384
+
+_STATUS = {
+    ERR_INVALID_ARG: "EIGER_ERR_INVALID_ARG",
+    ERR_CAPACITY: "EIGER_ERR_CAPACITY",
+    ERR_WORKSPACE: "EIGER_ERR_WORKSPACE",
+    ERR_TABLE_FULL: "EIGER_ERR_TABLE_FULL",
+    ERR_CUDA: "EIGER_ERR_CUDA",
+    ERR_INTERNAL: "EIGER_ERR_INTERNAL",
+}
+
+
+class EigerError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class StatsT(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("min", ctypes.c_int64), ("max", ctypes.c_int64),
+                ("estimate", ctypes.c_double), ("hll", ctypes.c_uint8 * HLL_M)]
+
+
+class StageT(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("ms", ctypes.c_float), ("launches", ctypes.c_int32),
+                ("bytes", ctypes.c_double)]
+
+
+class PlanT(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("bits1", ctypes.c_int32), ("bits2", ctypes.c_int32),
+                ("narrow", ctypes.c_int32), ("load_factor", ctypes.c_float),
+                ("selector", ctypes.c_int32), ("key_min", ctypes.c_int64),
+                ("key_max", ctypes.c_int64)]
+
+
+@dataclass
+class Stats:
+    n: int
+    min: int
+    max: int
+    estimate: float
+    hll: np.ndarray
+
+    @classmethod
+    def from_c(cls, s: StatsT) -> "Stats":
+        return cls(s.n, s.min, s.max, s.estimate, np.frombuffer(bytes(s.hll), np.uint8).copy())
+
+    def to_c(self) -> StatsT:
+        s = StatsT()
+        s.n, s.min, s.max, s.estimate = self.n, self.min, self.max, self.estimate
+        ctypes.memmove(s.hll, np.ascontiguousarray(self.hll, np.uint8).ctypes.data, HLL_M)
+        return s
+
+
+@dataclass
+class Plan:
+    variant: str
+    bits1: int = 0
+    bits2: int = 0
+    narrow: int = 0
+    load_factor: float = 0.5
+    selector: int = 0
+    key_min: int = 0
+    key_max: int = 0
+
+    @classmethod
+    def from_c(cls, p: PlanT) -> "Plan":
+        return cls(VARIANT_NAMES.get(p.variant, str(p.variant)), p.bits1, p.bits2, p.narrow,
+                   p.load_factor, p.selector, p.key_min, p.key_max)
+
+    def to_c(self) -> PlanT:
+        p = PlanT()
+        p.variant = VARIANTS[self.variant]
+        p.bits1, p.bits2, p.narrow = self.bits1, self.bits2, self.narrow
+        p.load_factor, p.selector = self.load_factor, self.selector
+        return p
+
+
+_lib = None
+
+# Every symbol include/eiger.h declares (checked against the header by the tests).
+SYMBOLS = ("eiger_stats_workspace", "eiger_stats", "eiger_plan", "eiger_join_workspace", "eiger_join",
+           "eiger_join_sum", "eiger_profile", "eiger_profile_read", "eiger_last_error",
+           "eiger_version")
+
+
+def load():
+    """Load libeiger.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    c = ctypes
+    vp, i64, i32, sz = c.c_void_p, c.c_int64, c.c_int32, c.c_size_t
+    lib.eiger_last_error.restype = c.c_char_p
+    lib.eiger_last_error.argtypes = []
+    lib.eiger_version.restype = c.c_char_p
+    lib.eiger_version.argtypes = []
+    lib.eiger_stats_workspace.restype = c.c_int
+    lib.eiger_stats_workspace.argtypes = [i64, c.c_int, c.POINTER(sz)]
+    lib.eiger_stats.restype = c.c_int
+    lib.eiger_stats.argtypes = [vp, i64, c.c_int, c.POINTER(StatsT), vp, sz, vp]
+    lib.eiger_plan.restype = c.c_int
+    lib.eiger_plan.argtypes = [c.POINTER(StatsT), c.POINTER(StatsT), i64, i64, c.c_int,
+                               c.POINTER(PlanT)]
+    lib.eiger_join_workspace.restype = c.c_int
+    lib.eiger_join_workspace.argtypes = [i64, i64, c.c_int, c.c_int, c.POINTER(PlanT), c.POINTER(sz)]
+    lib.eiger_join.restype = c.c_int
+    lib.eiger_join.argtypes = [c.c_int, vp, vp, i64, vp, vp, i64, i32, c.c_int, c.POINTER(PlanT),
+                               vp, vp, vp, vp, i64, c.POINTER(i64), vp, sz, c.POINTER(PlanT), vp]
+    lib.eiger_join_sum.restype = c.c_int
+    lib.eiger_join_sum.argtypes = [c.c_int, vp, vp, i64, vp, vp, i64, i32, c.c_int,
+                                   c.POINTER(PlanT), c.POINTER(i64), c.POINTER(i64), vp, sz,
+                                   c.POINTER(PlanT), vp]
+    lib.eiger_profile.restype = c.c_int
+    lib.eiger_profile.argtypes = [c.c_int]
+    lib.eiger_profile_read.restype = c.c_int
+    lib.eiger_profile_read.argtypes = [c.POINTER(StageT), c.c_int]
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise EigerError(status, load().eiger_last_error().decode())
+
+
+def last_error() -> str:
+    return load().eiger_last_error().decode()
+
+
+def version() -> str:
+    return load().eiger_version().decode()
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.int32:
+        return I32
+    if t.dtype == torch.int64:
+        return I64
+    raise TypeError(f"join keys must be int32 or int64, got {t.dtype}")
+
+
+def _ptr(t):
+    return None if t is None or t.numel() == 0 else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _variant(v) -> int:
+    return VARIANTS[v] if isinstance(v, str) else int(v)
+
+
+def _dev(t: torch.Tensor | None, device) -> torch.Tensor | None:
+    """Host tensors are copied to the device (the end-to-end path)."""
+    if t is None:
+        return None
+    t = t.contiguous()
+    return t if t.is_cuda else t.to(device, non_blocking=True)
+
+
+# ------------------------------------------------------------------ API
+
+def profile(enable: bool = True) -> None:
+    """eiger_profile: time every kernel launch of later calls on this thread."""
+    _check(load().eiger_profile(1 if enable else 0))
+
+
+def profile_read() -> list[tuple[str, float, int, float]]:
+    """(name, device ms, kernel launches, algorithmic bytes) of each stage of
+    the last call on this thread."""
+    lib = load()
+    n = lib.eiger_profile_read(None, 0)
+    buf = (StageT * max(n, 1))()
+    n = lib.eiger_profile_read(buf, n)
+    return [(buf[i].name.decode(), float(buf[i].ms), int(buf[i].launches), float(buf[i].bytes))
+            for i in range(n)]
+
+
+def stats_workspace(n: int, dtype: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().eiger_stats_workspace(n, dtype, ctypes.byref(out)))
+    return out.value
+
+
+def stats(keys: torch.Tensor, workspace: torch.Tensor | None = None, stream=None) -> Stats:
+    """eiger_stats: min, max, HyperLogLog++ registers and estimate of a key column."""
+    lib = load()
+    keys = _dev(keys, torch.device("cuda"))
+    dt = _dtype_code(keys)
+    n = keys.numel()
+    if workspace is None:
+        workspace = torch.empty(stats_workspace(n, dt), dtype=torch.uint8, device=keys.device)
+    out = StatsT()
+    _check(lib.eiger_stats(_ptr(keys), n, dt, ctypes.byref(out), _ptr(workspace), workspace.numel(),
+                           _stream(stream)))
+    return Stats.from_c(out)
+
+
+def plan(build: Stats, probe: Stats | None, nb: int, np_: int, dtype: int) -> Plan:
+    """eiger_plan: the rule-based selector (host only)."""
+    out = PlanT()
+    b = build.to_c()
+    p = probe.to_c() if probe is not None else None
+    _check(load().eiger_plan(ctypes.byref(b), ctypes.byref(p) if p is not None else None, nb, np_,
+                             dtype, ctypes.byref(out)))
+    return Plan.from_c(out)
+
+
+def join_workspace(nb: int, np_: int, dtype: int, variant="auto", knobs: Plan | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    k = knobs.to_c() if knobs is not None else None
+    _check(load().eiger_join_workspace(nb, np_, dtype, _variant(variant),
+                                       ctypes.byref(k) if k is not None else None, ctypes.byref(out)))
+    return out.value
+
+
+@dataclass
+class JoinResult:
+    count: int
+    build_idx: torch.Tensor | None
+    probe_idx: torch.Tensor | None
+    build_pay: torch.Tensor | None
+    probe_pay: torch.Tensor | None
+    plan: Plan
+
+
+def join_into(build_keys, probe_keys, *, build_pay=None, probe_pay=None, variant="auto",
+              knobs: Plan | None = None, out_bidx=None, out_pidx=None, out_bpay=None, out_ppay=None,
+              capacity: int = 0, workspace: torch.Tensor, stream=None):
+    """eiger_join into caller-allocated device outputs. Returns (status, count, plan)."""
+    lib = load()
+    dt = _dtype_code(build_keys)
+    pay_bytes = build_pay.element_size() if build_pay is not None else (
+        probe_pay.element_size() if probe_pay is not None else 0)
+    cnt = ctypes.c_int64(0)
+    used = PlanT()
+    k = knobs.to_c() if knobs is not None else None
+    st = lib.eiger_join(dt, _ptr(build_keys), _ptr(build_pay), build_keys.numel(), _ptr(probe_keys),
+                        _ptr(probe_pay), probe_keys.numel(), pay_bytes, _variant(variant),
+                        ctypes.byref(k) if k is not None else None, _ptr(out_bidx), _ptr(out_pidx),
+                        _ptr(out_bpay), _ptr(out_ppay), capacity, ctypes.byref(cnt),
+                        _ptr(workspace), workspace.numel() if workspace is not None else 0,
+                        ctypes.byref(used), _stream(stream))
+    return st, cnt.value, Plan.from_c(used)
+
+
+def join(build_keys: torch.Tensor, probe_keys: torch.Tensor, *, build_pay=None, probe_pay=None,
+         variant="auto", knobs: Plan | None = None, indices: bool = True, payloads: bool = False,
+         capacity: int | None = None, workspace: torch.Tensor | None = None, stream=None,
+         to_host: bool = False) -> JoinResult:
+    """eiger_join: all matching (build_idx, probe_idx) pairs, and optionally the
+    matched payloads. Host (CPU) inputs are copied to the GPU first; with
+    ``to_host`` the results are copied back. Retries once with the exact
+    capacity when the first guess (``capacity`` or |S|) is too small."""
+    dev = torch.device("cuda")
+    bk, pk = _dev(build_keys, dev), _dev(probe_keys, dev)
+    bp, pp = _dev(build_pay, dev), _dev(probe_pay, dev)
+    if _dtype_code(bk) != _dtype_code(pk):
+        raise TypeError("build and probe keys must share a dtype")
+    if workspace is None:
+        workspace = torch.empty(join_workspace(bk.numel(), pk.numel(), _dtype_code(bk), variant,
+                                               knobs), dtype=torch.uint8, device=dev)
+    cap = pk.numel() if capacity is None else capacity
+    for attempt in range(2):
+        c = max(cap, 1)
+        ob = torch.empty(c, dtype=torch.int32, device=dev) if indices else None
+        op = torch.empty(c, dtype=torch.int32, device=dev) if indices else None
+        obp = torch.empty(c, dtype=bp.dtype, device=dev) if payloads and bp is not None else None
+        opp = torch.empty(c, dtype=pp.dtype, device=dev) if payloads and pp is not None else None
+        st, n, used = join_into(bk, pk, build_pay=bp, probe_pay=pp, variant=variant, knobs=knobs,
+                                out_bidx=ob, out_pidx=op, out_bpay=obp, out_ppay=opp, capacity=cap,
+                                workspace=workspace, stream=stream)
+        if st == ERR_CAPACITY and attempt == 0:
+            cap = n
+            continue
+        _check(st)
+        break
+    cut = lambda t: None if t is None else (t[:n].cpu() if to_host else t[:n])
+    return JoinResult(n, cut(ob), cut(op), cut(obp), cut(opp), used)
+
+
+def join_sum(build_keys, build_pay, probe_keys, probe_pay, *, variant="auto",
+             knobs: Plan | None = None, workspace: torch.Tensor | None = None, stream=None):
+    """eiger_join_sum: (sum over matches of build_pay + probe_pay mod 2^64, |J|, plan)."""
+    lib = load()
+    dev = torch.device("cuda")
+    bk, pk = _dev(build_keys, dev), _dev(probe_keys, dev)
+    bp, pp = _dev(build_pay, dev), _dev(probe_pay, dev)
+    dt = _dtype_code(bk)
+    if bp.dtype != pp.dtype:
+        raise TypeError("payload columns must share a dtype")
+    if workspace is None:
+        workspace = torch.empty(join_workspace(bk.numel(), pk.numel(), dt, variant, knobs),
+                                dtype=torch.uint8, device=dev)
+    s = ctypes.c_int64(0)
+    cnt = ctypes.c_int64(0)
+    used = PlanT()
+    k = knobs.to_c() if knobs is not None else None
+    _check(lib.eiger_join_sum(dt, _ptr(bk), _ptr(bp), bk.numel(), _ptr(pk), _ptr(pp), pk.numel(),
+                              bp.element_size(), _variant(variant),
+                              ctypes.byref(k) if k is not None else None, ctypes.byref(s),
+                              ctypes.byref(cnt), _ptr(workspace), workspace.numel(),
+                              ctypes.byref(used), _stream(stream)))
+    return s.value, cnt.value, Plan.from_c(used)
