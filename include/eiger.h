@@ -183,6 +183,34 @@ eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* 
                             int64_t* out_sum, int64_t* out_count, void* d_workspace,
                             size_t ws_bytes, eiger_plan_t* plan_used, void* stream);
 
+/*
+ * eiger_join_static_noalloc -- the static non-partitioned join for callers that
+ * cannot allocate device memory. The paper has no counterpart; this entry
+ * point exists for code that may not call cudaMalloc or any allocator where it
+ * joins (a component whose device memory is owned by someone else's pool, a
+ * plug-in host that forbids allocation on its execution path), but can pass
+ * arrays it already owns.
+ * It computes exactly what eiger_join(..., EIGER_STATIC, ...) computes into
+ * d_out_bidx / d_out_pidx (uint32, `capacity` entries each, either may be NULL;
+ * same capacity and *out_count rules), without statistics, payloads or a
+ * workspace argument, and allocates nothing: its hash table and control block
+ * live in one file-scope device array of 8 MiB + 256 bytes that every GPU
+ * loading the library holds until the process exits.
+ * Limit: build sides up to 2^19 rows for int32 keys, 2^18 rows for int64 keys;
+ * larger ones return EIGER_ERR_INVALID_ARG before any GPU work.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture begins. All calls on a device share the array and each clears it on
+ * its stream first, so consecutive calls are independent, but calls whose
+ * work overlaps on the GPU (other streams, other threads) race on it.
+ * Synchronises `stream`. Errors: INVALID_ARG, CAPACITY, TABLE_FULL, CUDA,
+ * INTERNAL.
+ */
+eiger_status eiger_join_static_noalloc(eiger_dtype dtype, const void* d_bkeys, int64_t nb,
+                                       const void* d_pkeys, int64_t np, uint32_t* d_out_bidx,
+                                       uint32_t* d_out_pidx, int64_t capacity, int64_t* out_count,
+                                       void* stream);
+
 /* One timed stage (one kernel launch, or the three of a scan) of the last
    call (see eiger_profile). */
 typedef struct {

@@ -371,6 +371,11 @@ size_t join_workspace_bytes(int64_t nb, int64_t np, int dtype, int variant, cons
 
 }  // namespace
 
+namespace eiger {
+// Records `msg` as the calling thread's last error and returns `s`.
+eiger_status report_error(eiger_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace eiger
+
 extern "C" {
 
 const char* eiger_last_error(void) { return g_last_error.c_str(); }

@@ -22,6 +22,7 @@ struct ProfScope {
 };
 void prof_reset();
 void prof_set_matches(unsigned long long m);
+bool prof_set_enabled(bool on);  // returns the previous setting
 double match_bytes(const JoinOut& out);
 
 // ------------------------------------------------------------------ stats

@@ -76,6 +76,12 @@ double match_bytes(const JoinOut& out) {
 }
 int prof_count() { return g_prof.used; }
 
+bool prof_set_enabled(bool on) {
+    const bool was = g_prof.enabled;
+    g_prof.enabled = on;
+    return was;
+}
+
 }  // namespace eiger
 
 using namespace eiger;

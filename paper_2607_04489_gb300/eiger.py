@@ -108,8 +108,8 @@ _lib = None
 
 # Every symbol include/eiger.h declares (checked against the header by the tests).
 SYMBOLS = ("eiger_stats_workspace", "eiger_stats", "eiger_plan", "eiger_join_workspace", "eiger_join",
-           "eiger_join_sum", "eiger_profile", "eiger_profile_read", "eiger_last_error",
-           "eiger_version")
+           "eiger_join_sum", "eiger_join_static_noalloc", "eiger_profile", "eiger_profile_read",
+           "eiger_last_error", "eiger_version")
 
 
 def load():
@@ -142,6 +142,9 @@ def load():
     lib.eiger_join_sum.argtypes = [c.c_int, vp, vp, i64, vp, vp, i64, i32, c.c_int,
                                    c.POINTER(PlanT), c.POINTER(i64), c.POINTER(i64), vp, sz,
                                    c.POINTER(PlanT), vp]
+    lib.eiger_join_static_noalloc.restype = c.c_int
+    lib.eiger_join_static_noalloc.argtypes = [c.c_int, vp, i64, vp, i64, vp, vp, i64, c.POINTER(i64),
+                                              vp]
     lib.eiger_profile.restype = c.c_int
     lib.eiger_profile.argtypes = [c.c_int]
     lib.eiger_profile_read.restype = c.c_int
@@ -336,3 +339,17 @@ def join_sum(build_keys, build_pay, probe_keys, probe_pay, *, variant="auto",
                               ctypes.byref(cnt), _ptr(workspace), workspace.numel(),
                               ctypes.byref(used), _stream(stream)))
     return s.value, cnt.value, Plan.from_c(used)
+
+
+def join_static_noalloc_into(build_keys, probe_keys, out_bidx, out_pidx, capacity: int,
+                             stream=None):
+    """eiger_join_static_noalloc into caller-owned outputs: the static join
+    with its scratch in the library's fixed device array (for callers that
+    cannot allocate). Returns (status, count)."""
+    lib = load()
+    dt = _dtype_code(build_keys)
+    cnt = ctypes.c_int64(0)
+    st = lib.eiger_join_static_noalloc(dt, _ptr(build_keys), build_keys.numel(), _ptr(probe_keys),
+                                       probe_keys.numel(), _ptr(out_bidx), _ptr(out_pidx), capacity,
+                                       ctypes.byref(cnt), _stream(stream))
+    return st, cnt.value
