@@ -132,7 +132,101 @@ __device__ __forceinline__ void write_pay(void* p, int bytes, unsigned long long
         ((int64_t*)p)[i] = v;
 }
 
-__host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) {
+// ---------------------------------------------------------------- TMA bulk copies
+
+// Shared-memory address of a generic pointer into shared memory.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes mbarrier initialisation visible to the async (TMA) proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) writes to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One-dimensional bulk copy global -> shared, completing on `bar`. Both
+// addresses and `bytes` must be multiples of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `bar` with the given parity; false after
+// kSpinLimit polls (the caller reports kErrInternal and stops).
+constexpr uint32_t kSpinLimit = 1u << 24;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Tile copies: the elements [first, first + len) of a global array go to a
+// shared buffer so that element e lands at dst[lead + e], with
+// lead = (address of first mod 16) / sizeof(E). The 16-byte aligned body
+// [body_lo, body_hi) moves by one bulk copy; the few head and tail elements
+// outside it are copied with plain loads by the issuing thread before it
+// arrives on the barrier, so waiters see both. Nothing outside the array is
+// read. tile_copy_plan returns the bulk bytes for arrive.expect_tx.
+template <typename E>
+__device__ __forceinline__ uint32_t tile_copy_plan(const E* first, uint32_t len, uint32_t& lead,
+                                                   uint32_t& body_lo, uint32_t& body_hi) {
+    constexpr uint32_t V = 16 / sizeof(E);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(first);
+    lead = (uint32_t)((a & 15u) / sizeof(E));
+    uint32_t lo = lead ? V - lead : 0u;  // first element index of the aligned body
+    if (lo > len) lo = len;
+    uint32_t hi = lo + (len - lo) / V * V;
+    body_lo = lo;
+    body_hi = hi;
+    return (hi - lo) * (uint32_t)sizeof(E);
+}
+
+template <typename E>
+__device__ __forceinline__ void tile_copy_edges(E* dst, const E* first, uint32_t len, uint32_t lead,
+                                                uint32_t body_lo, uint32_t body_hi) {
+    for (uint32_t e = 0; e < body_lo; ++e) dst[lead + e] = first[e];
+    for (uint32_t e = body_hi; e < len; ++e) dst[lead + e] = first[e];
+}
+
+template <typename E>
+__device__ __forceinline__ void tile_copy_body(E* dst, const E* first, uint32_t lead, uint32_t body_lo,
+                                               uint32_t body_hi, uint64_t* bar) {
+    if (body_hi > body_lo)
+        bulk_load(dst + lead + body_lo, first + body_lo, (body_hi - body_lo) * (uint32_t)sizeof(E), bar);
+}
+
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) {
     return (x + a - 1) / a * a;
 }
 

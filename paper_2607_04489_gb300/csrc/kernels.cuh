@@ -116,7 +116,7 @@ PhjScratch phj_layout(Carve& c, int64_t nb, int64_t np, const PlanDev& plan);
 // Radix-partitions one side into s.key/idx[passes - 1] and fills
 // s.part_start. side: 0 build, 1 probe (only the probe side is range-tested).
 cudaError_t partition_side(const void* keys, int64_t n, int side, const PlanDev& plan,
-                           const PartSide& s, cudaStream_t stream);
+                           const PartSide& s, unsigned* err, cudaStream_t stream);
 cudaError_t phj_run(const JoinArgs& a, const PlanDev& plan, const PhjScratch& s, const JoinOut& out,
                     Ctrl* ctrl, cudaStream_t stream);
 

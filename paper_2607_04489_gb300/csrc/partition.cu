@@ -20,6 +20,7 @@
 // is dropped here) and the frame-of-reference narrowing; later passes read the
 // (key', row) pairs of the previous pass.
 #include <cstdio>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -27,8 +28,8 @@ namespace eiger {
 
 namespace {
 
-constexpr int kPartThreads = 256;
-constexpr int kPartItems = kPartTile / kPartThreads;  // 16 rows per thread
+constexpr int kPartThreads = 512;
+constexpr int kPartItems = kPartTile / kPartThreads;  // 8 rows per thread
 constexpr uint32_t kNoDigit = 0xFFFFFFFFu;
 
 constexpr int kScanThreads = 512;
@@ -132,26 +133,151 @@ __device__ uint32_t block_scan_smem(const uint32_t* in, uint32_t* out, uint32_t 
     return total;
 }
 
+// Input element type of a pass: raw keys in pass 1, (key', row) later.
 template <typename InKey, typename KeyT, bool FIRST>
-__global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey, KeyT> a) {
-    extern __shared__ uint32_t s_cnt[];
-    const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
-    const uint32_t nd = 1u << a.bits;
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+struct PassIn {
+    using E = typename std::conditional<FIRST, InKey, KeyT>::type;
+    static constexpr uint32_t kPad = 16 / sizeof(E);  // room for the 16-byte lead
+    static constexpr size_t kKeyBytes = align_up((kPartTile + kPad) * sizeof(E), 16);
+    static constexpr size_t kIdxBytes = FIRST ? 0 : align_up((kPartTile + 4) * sizeof(uint32_t), 16);
+    static constexpr size_t kBufBytes = kKeyBytes + kIdxBytes;
+};
+
+// Shared-memory tile ring: two input buffers, each filled by TMA bulk copies
+// one tile ahead of the one being processed, each with its mbarrier.
+template <typename InKey, typename KeyT, bool FIRST>
+struct TileRing {
+    using P = PassIn<InKey, KeyT, FIRST>;
+    using E = typename P::E;
+    uint64_t* bar;          // [2]
+    unsigned char* buf[2];  // keys, then (later passes) rows
+
+    __device__ E* keys(int b) const { return reinterpret_cast<E*>(buf[b]); }
+    __device__ uint32_t* rows(int b) const { return reinterpret_cast<uint32_t*>(buf[b] + P::kKeyBytes); }
+
+    __device__ static const E* key_src(const PartPass<InKey, KeyT>& a, uint32_t start) {
+        if constexpr (FIRST)
+            return a.raw + start;
+        else
+            return a.in_key + start;
+    }
+
+    // Warp 0 only: start loading tile t into buffer b. The lanes copy the few
+    // unaligned head/tail elements in parallel; lane 0 then arrives on the
+    // buffer's barrier with the bulk byte count and issues the bulk copies.
+    __device__ void issue(const PartPass<InKey, KeyT>& a, uint32_t t, int b) const {
+        const unsigned lane = lane_id();
         const Tile tl = get_tile(a, t);
-        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
-        __syncthreads();
-        KeyT kk[kPartItems];
-        bool ok[kPartItems];
-#pragma unroll
-        for (int j = 0; j < kPartItems; ++j) {
-            const uint32_t e = j * kPartThreads + threadIdx.x;
-            uint32_t id;
-            ok[j] = e < tl.len && part_load<InKey, KeyT, FIRST>(a, tl.start + e, kk[j], id);
+        const E* kf = key_src(a, tl.start);
+        uint32_t klead, klo, khi;
+        uint32_t bytes = tile_copy_plan(kf, tl.len, klead, klo, khi);
+        edges_warp(keys(b), kf, tl.len, klead, klo, khi, lane);
+        uint32_t ilead = 0, ilo = 0, ihi = 0;
+        const uint32_t* rf = nullptr;
+        if constexpr (!FIRST) {
+            rf = a.in_idx + tl.start;
+            bytes += tile_copy_plan(rf, tl.len, ilead, ilo, ihi);
+            edges_warp(rows(b), rf, tl.len, ilead, ilo, ihi, lane);
         }
-#pragma unroll
-        for (int j = 0; j < kPartItems; ++j)
-            if (ok[j]) atomicAdd(&s_cnt[digit_of(kk[j], a.dshift, a.dmask)], 1u);
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[b], bytes);
+            tile_copy_body(keys(b), kf, klead, klo, khi, &bar[b]);
+            if constexpr (!FIRST) tile_copy_body(rows(b), rf, ilead, ilo, ihi, &bar[b]);
+        }
+    }
+
+    // Lane l of the issuing warp copies head element l and tail element l.
+    template <typename T>
+    __device__ static void edges_warp(T* dst, const T* first, uint32_t len, uint32_t lead, uint32_t lo,
+                                      uint32_t hi, unsigned lane) {
+        if (lane < lo) dst[lead + lane] = first[lane];
+        if (hi + lane < len) dst[lead + hi + lane] = first[hi + lane];
+    }
+};
+
+template <typename E>
+__device__ __forceinline__ uint32_t lead_of(const E* first) {
+    return (uint32_t)((reinterpret_cast<uintptr_t>(first) & 15u) / sizeof(E));
+}
+
+// Decodes element e of the current tile: applies the range test and the
+// narrowing in pass 1. Returns false for a dropped row.
+template <typename InKey, typename KeyT, bool FIRST>
+__device__ __forceinline__ bool tile_key(const PartPass<InKey, KeyT>& a,
+                                         const typename PassIn<InKey, KeyT, FIRST>::E* kbuf, uint32_t e,
+                                         KeyT& k) {
+    if constexpr (FIRST) {
+        const int64_t key = (int64_t)kbuf[e];
+        if (a.check_range && (key < a.rng.lo || key > a.rng.hi)) return false;
+        k = KeyCodec<KeyT>::encode(key, a.rng.offset);
+    } else {
+        k = kbuf[e];
+    }
+    return true;
+}
+
+template <typename InKey, typename KeyT, bool FIRST>
+__device__ __forceinline__ TileRing<InKey, KeyT, FIRST> ring_setup(unsigned char* smem, size_t off) {
+    using P = PassIn<InKey, KeyT, FIRST>;
+    TileRing<InKey, KeyT, FIRST> r;
+    r.bar = reinterpret_cast<uint64_t*>(smem);
+    r.buf[0] = smem + off;
+    r.buf[1] = smem + off + P::kBufBytes;
+    if (threadIdx.x == 0) {
+        mbar_init(&r.bar[0], 1);
+        mbar_init(&r.bar[1], 1);
+        fence_mbar_init();
+    }
+    return r;
+}
+
+// After a failed bounded wait: record the error and wait (bounded) for the
+// copy into the other buffer, so no TMA write lands after the CTA exits.
+template <typename InKey, typename KeyT, bool FIRST>
+__device__ void ring_abort(const TileRing<InKey, KeyT, FIRST>& r, int other, uint32_t parity,
+                           bool other_pending, unsigned* err) {
+    if (threadIdx.x == 0) {
+        atomicOr(err, kErrInternal);
+        if (other_pending) mbar_wait(&r.bar[other], parity);
+    }
+}
+
+template <typename InKey, typename KeyT, bool FIRST>
+__host__ __device__ constexpr size_t hist_smem_bytes(int bits) {
+    return align_up(16 + ((size_t)1 << bits) * sizeof(uint32_t), 16) +
+           2 * PassIn<InKey, KeyT, FIRST>::kBufBytes;
+}
+
+template <typename InKey, typename KeyT, bool FIRST>
+__global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey, KeyT> a, unsigned* err) {
+    using Ring = TileRing<InKey, KeyT, FIRST>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t nd = 1u << a.bits;
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + 16);
+    const Ring ring = ring_setup<InKey, KeyT, FIRST>(smem, align_up(16 + (size_t)nd * 4, 16));
+    __syncthreads();
+    const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
+    uint32_t t = blockIdx.x;
+    if (threadIdx.x < kWarp && t < ntiles) ring.issue(a, t, 0);
+    for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const int b = it & 1;
+        const uint32_t tn = t + gridDim.x;
+        if (threadIdx.x < kWarp && tn < ntiles) ring.issue(a, tn, b ^ 1);
+        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
+        const bool ok = mbar_wait(&ring.bar[b], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            ring_abort(ring, b ^ 1, ((it + 1) >> 1) & 1, tn < ntiles, err);
+            return;
+        }
+        const Tile tl = get_tile(a, t);
+        const auto* kbuf = ring.keys(b) + lead_of(Ring::key_src(a, tl.start));
+#pragma unroll 4
+        for (uint32_t e = threadIdx.x; e < tl.len; e += kPartThreads) {
+            KeyT k;
+            if (tile_key<InKey, KeyT, FIRST>(a, kbuf, e, k)) atomicAdd(&s_cnt[digit_of(k, a.dshift, a.dmask)], 1u);
+        }
         __syncthreads();
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x)
             a.counts[count_index(tl, t, d, a.bits)] = s_cnt[d];
@@ -159,39 +285,56 @@ __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey,
     }
 }
 
-template <typename KeyT>
+template <typename InKey, typename KeyT, bool FIRST>
 __host__ __device__ constexpr size_t scatter_smem_bytes(int bits) {
-    return align_up(3 * ((size_t)1 << bits) * sizeof(uint32_t), 16) +
-           (size_t)kPartTile * (sizeof(KeyT) + sizeof(uint32_t));
+    return align_up(16 + 3 * ((size_t)1 << bits) * sizeof(uint32_t), 16) +
+           2 * PassIn<InKey, KeyT, FIRST>::kBufBytes +
+           align_up((size_t)kPartTile * sizeof(KeyT), 16) + (size_t)kPartTile * sizeof(uint32_t);
 }
 
 template <typename InKey, typename KeyT, bool FIRST>
-__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InKey, KeyT> a) {
+__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InKey, KeyT> a, unsigned* err) {
+    using Ring = TileRing<InKey, KeyT, FIRST>;
+    using P = PassIn<InKey, KeyT, FIRST>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_warp[kPartThreads / kWarp];
     __shared__ uint32_t s_kept;
     const uint32_t nd = 1u << a.bits;
-    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + 16);
     uint32_t* s_start = s_cnt + nd;
     uint32_t* s_goff = s_start + nd;
-    KeyT* s_key = reinterpret_cast<KeyT*>(smem + align_up(3 * (size_t)nd * sizeof(uint32_t), 16));
-    uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_key + kPartTile);
+    const size_t ring_off = align_up(16 + 3 * (size_t)nd * 4, 16);
+    const Ring ring = ring_setup<InKey, KeyT, FIRST>(smem, ring_off);
+    KeyT* s_key = reinterpret_cast<KeyT*>(smem + ring_off + 2 * P::kBufBytes);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(s_key) +
+                                                  align_up((size_t)kPartTile * sizeof(KeyT), 16));
+    __syncthreads();
 
     const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const Tile tl = get_tile(a, t);
+    uint32_t t = blockIdx.x;
+    if (threadIdx.x < kWarp && t < ntiles) ring.issue(a, t, 0);
+    for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const int b = it & 1;
+        const uint32_t tn = t + gridDim.x;
+        if (threadIdx.x < kWarp && tn < ntiles) ring.issue(a, tn, b ^ 1);
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
-        __syncthreads();
+        const bool ok = mbar_wait(&ring.bar[b], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            ring_abort(ring, b ^ 1, ((it + 1) >> 1) & 1, tn < ntiles, err);
+            return;
+        }
+        const Tile tl = get_tile(a, t);
+        const auto* kbuf = ring.keys(b) + lead_of(Ring::key_src(a, tl.start));
+        const uint32_t* rbuf = nullptr;
+        if constexpr (!FIRST) rbuf = ring.rows(b) + lead_of(a.in_idx + tl.start);
 
-        KeyT kk[kPartItems];
-        uint32_t ii[kPartItems];
         uint32_t dr[kPartItems];  // (rank << 12) | digit, or kNoDigit
 #pragma unroll
         for (int j = 0; j < kPartItems; ++j) {
             const uint32_t e = j * kPartThreads + threadIdx.x;
             dr[j] = kNoDigit;
-            if (e < tl.len && part_load<InKey, KeyT, FIRST>(a, tl.start + e, kk[j], ii[j]))
-                dr[j] = digit_of(kk[j], a.dshift, a.dmask);
+            KeyT k;
+            if (e < tl.len && tile_key<InKey, KeyT, FIRST>(a, kbuf, e, k)) dr[j] = digit_of(k, a.dshift, a.dmask);
         }
 #pragma unroll
         for (int j = 0; j < kPartItems; ++j)
@@ -207,9 +350,15 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
 #pragma unroll
         for (int j = 0; j < kPartItems; ++j) {
             if (dr[j] != kNoDigit) {
+                const uint32_t e = j * kPartThreads + threadIdx.x;
                 const uint32_t pos = s_start[dr[j] & 0xFFFu] + (dr[j] >> 12);
-                s_key[pos] = kk[j];
-                s_idx[pos] = ii[j];
+                KeyT k;
+                tile_key<InKey, KeyT, FIRST>(a, kbuf, e, k);
+                s_key[pos] = k;
+                if constexpr (FIRST)
+                    s_idx[pos] = tl.start + e;
+                else
+                    s_idx[pos] = rbuf[e];
             }
         }
         __syncthreads();
@@ -354,20 +503,29 @@ __global__ void __launch_bounds__(1024)
     const uint32_t total = block_scan_smem(s_nt, s_base, nseg, s_warp);
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < nseg; s += blockDim.x) {
-        const uint32_t nt = s_nt[s], base = s_base[s];
-        segs[s].tile_base = base;
-        segs[s].ntiles = nt;
-        const uint32_t st = segs[s].start, sz = segs[s].size;
-        for (uint32_t k = 0; k < nt; ++k) {
-            Tile tl;
-            tl.start = st + k * kPartTile;
-            const uint32_t rest = sz - k * kPartTile;
-            tl.len = rest < (uint32_t)kPartTile ? rest : (uint32_t)kPartTile;
-            tl.seg = s;
-            tl.tile_base = base;
-            tl.ntiles_seg = nt;
-            tiles[base + k] = tl;
+        segs[s].tile_base = s_base[s];
+        segs[s].ntiles = s_nt[s];
+    }
+    // every thread fills tiles; the segment of tile k is the last s with
+    // s_base[s] <= k among segments that have tiles (binary search in smem)
+    for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
+        uint32_t lo = 0, hi = nseg;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_base[mid] <= k) lo = mid; else hi = mid;
         }
+        // (an empty segment shares its base with the next one, so the last
+        // segment whose base is <= k always has tiles)
+        const uint32_t j = k - s_base[lo];
+        const uint32_t st = segs[lo].start, sz = segs[lo].size;
+        Tile tl;
+        tl.start = st + j * kPartTile;
+        const uint32_t rest = sz - j * kPartTile;
+        tl.len = rest < (uint32_t)kPartTile ? rest : (uint32_t)kPartTile;
+        tl.seg = lo;
+        tl.tile_base = s_base[lo];
+        tl.ntiles_seg = s_nt[lo];
+        tiles[k] = tl;
     }
     if (threadIdx.x == 0) *ntiles2 = total;
 }
@@ -422,43 +580,44 @@ cudaError_t scan_counts(uint32_t* counts, ScanLen L, size_t max_len, uint32_t* b
 // One partitioning pass over n rows. Algorithmic bytes per launch: the
 // histogram reads each key once; the scatter reads each (key, row) once and
 // writes each kept (key', row) once; the scan reads and writes the counts.
-template <typename InKey, typename KeyT>
-cudaError_t run_pass(PartPass<InKey, KeyT> a, bool first, size_t max_tiles, const PartSide& s,
-                     uint32_t* total, const DevInfo& di, cudaStream_t stream, const char* side_name) {
+template <typename InKey, typename KeyT, bool FIRST>
+cudaError_t run_pass(PartPass<InKey, KeyT> a, size_t max_tiles, const PartSide& s, uint32_t* total,
+                     unsigned* err, const DevInfo& di, cudaStream_t stream, const char* side_name) {
     cudaError_t e;
-    const size_t hsmem = ((size_t)1 << a.bits) * sizeof(uint32_t);
-    const size_t ssmem = scatter_smem_bytes<KeyT>(a.bits);
-    auto hist = first ? part_hist_kernel<InKey, KeyT, true> : part_hist_kernel<InKey, KeyT, false>;
-    auto scat = first ? part_scatter_kernel<InKey, KeyT, true> : part_scatter_kernel<InKey, KeyT, false>;
+    const size_t hsmem = hist_smem_bytes<InKey, KeyT, FIRST>(a.bits);
+    const size_t ssmem = scatter_smem_bytes<InKey, KeyT, FIRST>(a.bits);
+    auto hist = part_hist_kernel<InKey, KeyT, FIRST>;
+    auto scat = part_scatter_kernel<InKey, KeyT, FIRST>;
     if ((e = set_smem(hist, hsmem)) != cudaSuccess) return e;
     if ((e = set_smem(scat, ssmem)) != cudaSuccess) return e;
     const double n = (double)a.n;
-    const double in_key = first ? (double)sizeof(InKey) : (double)sizeof(KeyT);
+    const double in_key = FIRST ? (double)sizeof(InKey) : (double)sizeof(KeyT);
     const double tuple = (double)(sizeof(KeyT) + sizeof(uint32_t));
-    const double in_tuple = first ? (double)sizeof(InKey) : tuple;
+    const double in_tuple = FIRST ? (double)sizeof(InKey) : tuple;
+    const char* pn = FIRST ? "p1" : "p2";
     char name[32];
     {
-        snprintf(name, sizeof name, "part_hist.%s.%s", first ? "p1" : "p2", side_name);
+        snprintf(name, sizeof name, "part_hist.%s.%s", pn, side_name);
         ProfScope ps(name, n * in_key, stream);
-        hist<<<occupancy_grid(hist, kPartThreads, hsmem, di, max_tiles), kPartThreads, hsmem, stream>>>(a);
+        hist<<<occupancy_grid(hist, kPartThreads, hsmem, di, max_tiles), kPartThreads, hsmem, stream>>>(a, err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     ScanLen L{max_tiles << a.bits, a.tiles ? a.ntiles_dev : nullptr, a.bits};
     {
-        snprintf(name, sizeof name, "part_scan.%s.%s", first ? "p1" : "p2", side_name);
+        snprintf(name, sizeof name, "part_scan.%s.%s", pn, side_name);
         ProfScope ps(name, 12.0 * (double)(max_tiles << a.bits), stream, 0.0, 3);
         if ((e = scan_counts(a.counts, L, max_tiles << a.bits, s.block_sums, total, stream)) != cudaSuccess)
             return e;
     }
-    snprintf(name, sizeof name, "part_scatter.%s.%s", first ? "p1" : "p2", side_name);
+    snprintf(name, sizeof name, "part_scatter.%s.%s", pn, side_name);
     ProfScope ps(name, n * (in_tuple + tuple), stream);
-    scat<<<occupancy_grid(scat, kPartThreads, ssmem, di, max_tiles), kPartThreads, ssmem, stream>>>(a);
+    scat<<<occupancy_grid(scat, kPartThreads, ssmem, di, max_tiles), kPartThreads, ssmem, stream>>>(a, err);
     return cudaGetLastError();
 }
 
 template <typename InKey, typename KeyT>
 cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanDev& plan,
-                            const PartSide& s, const DevInfo& di, cudaStream_t stream) {
+                            const PartSide& s, unsigned* err, const DevInfo& di, cudaStream_t stream) {
     const int passes = plan.variant == 3 ? 2 : 1;
     const int b1 = plan.bits1, b2 = passes == 2 ? plan.bits2 : 0;
     const uint32_t ntiles1 = (n + kPartTile - 1) / kPartTile;
@@ -478,13 +637,16 @@ cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanD
     a.tiles = nullptr;
     a.ntiles_fixed = ntiles1;
     const char* sn = side == 0 ? "build" : "probe";
-    if ((e = run_pass(a, true, ntiles1, s, s.total, di, stream, sn)) != cudaSuccess) return e;
+    if ((e = run_pass<InKey, KeyT, true>(a, ntiles1, s, s.total, err, di, stream, sn)) != cudaSuccess)
+        return e;
 
     if (passes == 2) {
-        ProfScope ps("seg_tiles", 0.0, stream);
-        seg_tiles_kernel<<<1, 1024, 0, stream>>>(s.counts, ntiles1, b1, s.total, s.segs, s.tiles,
-                                                 s.total + 2);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        {
+            ProfScope ps("seg_tiles", 0.0, stream);
+            seg_tiles_kernel<<<1, 1024, 0, stream>>>(s.counts, ntiles1, b1, s.total, s.segs, s.tiles,
+                                                     s.total + 2);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         PartPass<InKey, KeyT> b{};
         b.in_key = static_cast<const KeyT*>(s.key[0]);
         b.in_idx = s.idx[0];
@@ -500,7 +662,9 @@ cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanD
         b.tiles = s.tiles;
         b.ntiles_dev = s.total + 2;
         const size_t max_tiles2 = (size_t)ntiles1 + ((size_t)1 << b1);
-        if ((e = run_pass(b, false, max_tiles2, s, s.total + 1, di, stream, sn)) != cudaSuccess) return e;
+        if ((e = run_pass<InKey, KeyT, false>(b, max_tiles2, s, s.total + 1, err, di, stream, sn)) !=
+            cudaSuccess)
+            return e;
     }
     const uint32_t P = 1u << (b1 + b2);
     const int threads = 256;
@@ -522,12 +686,8 @@ size_t part_counts_len(int64_t n, int b1, int b2, int passes) {
 
 size_t part_scan_blocks(size_t counts_len) { return (counts_len + kScanChunk - 1) / kScanChunk + 1; }
 
-size_t part_scatter_smem(int bits, int key32) {
-    return key32 ? scatter_smem_bytes<uint32_t>(bits) : scatter_smem_bytes<uint64_t>(bits);
-}
-
 cudaError_t partition_side(const void* keys, int64_t n, int side, const PlanDev& plan,
-                           const PartSide& s, cudaStream_t stream) {
+                           const PartSide& s, unsigned* err, cudaStream_t stream) {
     DevInfo di;
     cudaError_t e = current_device_info(&di);
     if (e != cudaSuccess) return e;
@@ -535,12 +695,12 @@ cudaError_t partition_side(const void* keys, int64_t n, int side, const PlanDev&
     if (plan.key32) {
         if (plan.dtype == 0)
             return partition_typed<int32_t, uint32_t>(static_cast<const int32_t*>(keys), nn, side, plan,
-                                                      s, di, stream);
+                                                      s, err, di, stream);
         return partition_typed<int64_t, uint32_t>(static_cast<const int64_t*>(keys), nn, side, plan, s,
-                                                  di, stream);
+                                                  err, di, stream);
     }
-    return partition_typed<int64_t, uint64_t>(static_cast<const int64_t*>(keys), nn, side, plan, s, di,
-                                              stream);
+    return partition_typed<int64_t, uint64_t>(static_cast<const int64_t*>(keys), nn, side, plan, s, err,
+                                              di, stream);
 }
 
 }  // namespace eiger

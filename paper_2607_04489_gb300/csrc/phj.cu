@@ -26,9 +26,17 @@ size_t part_scan_blocks(size_t counts_len);
 namespace {
 
 constexpr int kJoinThreads = 512;
-constexpr int kJoinItems = 2;
-constexpr int kJoinStage = 2048;  // >= kJoinThreads * kJoinItems
-constexpr uint32_t kBuildCap = 4096;
+constexpr int kMaxRows = 8;                       // rows per thread per round (32-bit keys)
+constexpr int kJoinStage = kJoinThreads * kMaxRows;  // a unique-key round never spills
+constexpr uint32_t kBuildCap = 4096;              // build rows per shared-memory table
+
+// Rows each thread keeps in flight per round: 8 for 32-bit keys, 4 for 64-bit
+// keys (register budget of two 512-thread CTAs per SM).
+template <typename KeyT>
+struct Rows {
+    static constexpr int kN = sizeof(KeyT) == 4 ? 8 : 4;
+    static constexpr uint32_t kRound = kJoinThreads * kN;
+};
 constexpr uint32_t kProbeChunk = 16384;
 constexpr uint32_t kTableMax = 2 * kBuildCap;
 constexpr uint32_t kEmptyRow = 0xFFFFFFFFu;
@@ -45,61 +53,88 @@ struct JoinIn {
     uint32_t P;
 };
 
-// One block: item counts per partition, exclusive prefix, total.
-__global__ void __launch_bounds__(1024)
-    items_kernel(const uint32_t* __restrict__ bstart, const uint32_t* __restrict__ pstart, uint32_t P,
-                 unsigned long long* __restrict__ prefix, Ctrl* ctrl) {
-    __shared__ unsigned long long s_warp[1024 / kWarp];
-    const uint32_t per = (P + blockDim.x - 1) / blockDim.x;
-    uint32_t beg = threadIdx.x * per;
-    if (beg > P) beg = P;
-    uint32_t end = beg + per;
-    if (end > P) end = P;
-    unsigned long long local = 0;
-    for (uint32_t p = beg; p < end; ++p) {
+// Work items of partition p: build chunks x probe chunks (none if a side is empty).
+__global__ void items_count_kernel(const uint32_t* __restrict__ bstart, const uint32_t* __restrict__ pstart,
+                                   uint32_t P, unsigned long long* __restrict__ count) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         const uint32_t bs = bstart[p + 1] - bstart[p];
         const uint32_t ps = pstart[p + 1] - pstart[p];
-        const unsigned long long c =
-            (bs && ps) ? (unsigned long long)((bs + kBuildCap - 1) / kBuildCap) *
-                             ((ps + kProbeChunk - 1) / kProbeChunk)
-                       : 0ull;
-        prefix[p] = c;
-        local += c;
+        count[p] = (bs && ps) ? (unsigned long long)((bs + kBuildCap - 1) / kBuildCap) *
+                                    ((ps + kProbeChunk - 1) / kProbeChunk)
+                              : 0ull;
     }
-    unsigned long long x = local;
+}
+
+// One block: exclusive scan of the item counts in place, 4096 per chunk with
+// coalesced loads and stores; prefix[P] and ctrl->nitems get the total.
+__global__ void __launch_bounds__(1024)
+    items_scan_kernel(unsigned long long* __restrict__ prefix, uint32_t P, Ctrl* ctrl) {
+    constexpr int kPer = 4;
+    constexpr uint32_t kChunk = 1024 * kPer;
+    __shared__ unsigned long long s_buf[kChunk];
+    __shared__ unsigned long long s_warp[1024 / kWarp];
     const unsigned lane = lane_id();
-#pragma unroll
-    for (int o = 1; o < kWarp; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if ((int)lane >= o) x += y;
-    }
     const int warp = threadIdx.x / kWarp;
-    if ((int)lane == kWarp - 1) s_warp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned long long v = s_warp[lane];
+    unsigned long long carry = 0;
+    for (uint32_t base = 0; base < P; base += kChunk) {
+        for (uint32_t i = threadIdx.x; i < kChunk; i += blockDim.x)
+            s_buf[i] = base + i < P ? prefix[base + i] : 0ull;
+        __syncthreads();
+        unsigned long long local = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) local += s_buf[threadIdx.x * kPer + j];
+        unsigned long long x = local;
 #pragma unroll
         for (int o = 1; o < kWarp; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
-            if ((int)lane >= o) v += y;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
         }
-        s_warp[lane] = v;
+        if ((int)lane == kWarp - 1) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long v = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < kWarp; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+                if ((int)lane >= o) v += y;
+            }
+            s_warp[lane] = v;
+        }
+        __syncthreads();
+        unsigned long long run = carry + (warp ? s_warp[warp - 1] : 0ull) + x - local;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const unsigned long long c = s_buf[threadIdx.x * kPer + j];
+            s_buf[threadIdx.x * kPer + j] = run;
+            run += c;
+        }
+        carry += s_warp[kWarp - 1];
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < kChunk && base + i < P; i += blockDim.x) prefix[base + i] = s_buf[i];
+        __syncthreads();
     }
-    __syncthreads();
-    unsigned long long run = (warp ? s_warp[warp - 1] : 0ull) + x - local;
-    for (uint32_t p = beg; p < end; ++p) {
-        const unsigned long long c = prefix[p];
-        prefix[p] = run;
-        run += c;
-    }
-    if (threadIdx.x == blockDim.x - 1) {
-        prefix[P] = s_warp[kWarp - 1];
-        ctrl->nitems = s_warp[kWarp - 1];
+    if (threadIdx.x == 0) {
+        prefix[P] = carry;
+        ctrl->nitems = carry;
     }
 }
 
 template <typename KeyT>
 struct SmemTable;
+
+// Home slot of a key in a table of `tsize` slots. The partition was chosen by
+// the top bits of the hash, so the hash is first remixed by an odd multiplier
+// (which carries its low bits into the high bits) and then mapped onto
+// [0, tsize) by a multiply-shift range reduction.
+template <typename KeyT>
+__device__ __forceinline__ uint32_t home_slot(KeyT k, uint32_t tsize) {
+    const uint32_t h = (uint32_t)KeyCodec<KeyT>::hash(k) * 0x9E3779B1u;
+    return (uint32_t)(((unsigned long long)h * tsize) >> 32);
+}
+
+__device__ __forceinline__ uint32_t next_slot(uint32_t s, uint32_t tsize) {
+    return s + 1 == tsize ? 0u : s + 1;
+}
 
 // 32-bit keys: one packed 64-bit word per slot, claimed by CAS.
 template <>
@@ -108,8 +143,11 @@ struct SmemTable<uint32_t> {
     unsigned long long* slot;
     __device__ void bind(unsigned char* smem) { slot = reinterpret_cast<unsigned long long*>(smem); }
     __device__ void clear(uint32_t i) { slot[i] = kEmptySlot; }
-    __device__ bool insert(uint32_t s, uint32_t k, uint32_t row) {
-        return atomicCAS(slot + s, kEmptySlot, ((unsigned long long)k << 32) | row) == kEmptySlot;
+    // 1: inserted; 0: slot taken by another key; -1: slot taken by the same key
+    __device__ int insert(uint32_t s, uint32_t k, uint32_t row) {
+        const unsigned long long prev = atomicCAS(slot + s, kEmptySlot, ((unsigned long long)k << 32) | row);
+        if (prev == kEmptySlot) return 1;
+        return (uint32_t)(prev >> 32) == k ? -1 : 0;
     }
     // 0: empty (chain ends), 1: occupied, other key, 2: match
     __device__ int probe(uint32_t s, uint32_t k, uint32_t& row) const {
@@ -131,10 +169,12 @@ struct SmemTable<uint64_t> {
         row = reinterpret_cast<uint32_t*>(smem + (size_t)kTableMax * 8);
     }
     __device__ void clear(uint32_t i) { row[i] = kEmptyRow; }
-    __device__ bool insert(uint32_t s, uint64_t k, uint32_t r) {
-        if (atomicCAS(row + s, kEmptyRow, r) != kEmptyRow) return false;
+    // 1: inserted; 0: slot taken (its key may still be in flight, so equal
+    // keys are not detected here: 64-bit tables always take the general path)
+    __device__ int insert(uint32_t s, uint64_t k, uint32_t r) {
+        if (atomicCAS(row + s, kEmptyRow, r) != kEmptyRow) return 0;
         key[s] = k;
-        return true;
+        return 1;
     }
     __device__ int probe(uint32_t s, uint64_t k, uint32_t& r) const {
         const uint32_t v = row[s];
@@ -144,98 +184,265 @@ struct SmemTable<uint64_t> {
     }
 };
 
+// Rows of a probe round: kRows per thread, strided by the block size so every
+// load instruction of a warp reads 32 consecutive rows.
+template <typename KeyT>
+struct RoundRegs {
+    KeyT k[Rows<KeyT>::kN];
+    uint32_t id[Rows<KeyT>::kN];
+};
+
+template <typename KeyT>
+__device__ __forceinline__ void load_round(RoundRegs<KeyT>& r, const KeyT* __restrict__ key,
+                                           const uint32_t* __restrict__ idx, uint32_t base,
+                                           uint32_t n) {
+#pragma unroll
+    for (int j = 0; j < Rows<KeyT>::kN; ++j) {
+        const uint32_t i = base + j * kJoinThreads + threadIdx.x;
+        if (i < n) {
+            r.k[j] = __ldcs(key + i);
+            r.id[j] = __ldcs(idx + i);
+        }
+    }
+}
+
+constexpr uint32_t kHole = 0xFFFFFFFFu;  // stage position without a match
+
+// Warp-collective: the last partition p in [0, P) with prefix[p] <= item
+// (prefix is non-decreasing, prefix[0] = 0). Each step tests 32 evenly spaced
+// pivots at once, so 2^15 partitions take three dependent loads.
+__device__ __forceinline__ uint32_t find_partition(const unsigned long long* __restrict__ prefix,
+                                                   uint32_t P, unsigned long long item) {
+    const unsigned lane = lane_id();
+    uint32_t lo = 0, hi = P;
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + kWarp - 1) / kWarp;
+        const uint32_t piv = lo + lane * step;
+        const bool le = piv < hi && prefix[piv] <= item;
+        const unsigned m = __ballot_sync(0xffffffffu, le);
+        const uint32_t last = 31 - __clz(m);  // lane 0 always qualifies
+        lo = lo + last * step;
+        hi = lo + step < hi ? lo + step : hi;
+    }
+    return lo;
+}
+constexpr int kJoinWarps = kJoinThreads / kWarp;
+
+// Block-collective flush of a positional stage: position j * kJoinThreads + t
+// holds the match of thread t's row j, or kHole. Ballots give every match its
+// rank within its (row j, warp) group, one scan over the kN x warps group
+// counts places the groups, one global atomic reserves the round's output,
+// and each warp then writes its group to consecutive output positions.
+template <int kN>
+__device__ __forceinline__ void flush_positional(Stage<kJoinStage>& st, uint32_t* s_grp,
+                                                 const JoinOut& out, Ctrl* ctrl) {
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x / kWarp;
+    unsigned ball[kN];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kN; ++j) {
+        ball[j] = __ballot_sync(0xffffffffu, st.b[j * kJoinThreads + threadIdx.x] != kHole);
+        if (lane == 0) s_grp[j * kJoinWarps + w] = __popc(ball[j]);
+    }
+    __syncthreads();
+    if (w == 0) {
+        // exclusive scan of kN * kJoinWarps group counts, kN * 16 / 32 per lane
+        constexpr int kPer = (kN * kJoinWarps + kWarp - 1) / kWarp;
+        uint32_t v[kPer], local = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int e = lane * kPer + i;
+            v[i] = e < kN * kJoinWarps ? s_grp[e] : 0u;
+            local += v[i];
+        }
+        uint32_t x = local;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        uint32_t run = x - local;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int e = lane * kPer + i;
+            if (e < kN * kJoinWarps) s_grp[e] = run;
+            run += v[i];
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, x, kWarp - 1);
+        if (lane == 0) st.base = total ? atomicAdd(&ctrl->cursor, (unsigned long long)total) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long base = st.base;
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < kN; ++j) {
+        const uint32_t i = j * kJoinThreads + threadIdx.x;
+        if (ball[j] & (1u << lane))
+            write_match(out, base + s_grp[j * kJoinWarps + w] + __popc(ball[j] & lt), st.b[i], st.p[i]);
+    }
+    __syncthreads();
+}
+
 template <typename KeyT, bool AGG>
-__global__ void __launch_bounds__(kJoinThreads)
+__global__ void __launch_bounds__(kJoinThreads, 2)
     phj_join_kernel(JoinIn<KeyT> a, JoinOut out, Ctrl* ctrl) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Stage<kJoinStage> st;
-    __shared__ unsigned long long s_item;
+    __shared__ uint32_t s_grp[kMaxRows * kJoinWarps];
+    __shared__ unsigned long long s_next_item;
+    __shared__ uint32_t s_next_part;
+    constexpr int kN = Rows<KeyT>::kN;
+    constexpr uint32_t kRound = Rows<KeyT>::kRound;
     SmemTable<KeyT> tab;
     tab.bind(smem);
     if (threadIdx.x == 0) st.count = 0;
     AggState agg{0ull, 0ull};
     const unsigned long long nitems = ctrl->nitems;
 
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl->next_item, 1ull);
-        __syncthreads();
-        const unsigned long long item = s_item;
-        if (item >= nitems) break;
-
-        // partition p: the last p with prefix[p] <= item
-        uint32_t lo = 0, hi = a.P;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (a.item_prefix[mid] <= item) lo = mid; else hi = mid;
+    // Work items are claimed one ahead: the claim for the next item is issued
+    // when an item starts, and its partition is looked up by warp 0 after the
+    // build, so neither round trip sits between two items.
+    if (threadIdx.x < kWarp) {
+        unsigned long long it0 = 0;
+        if (threadIdx.x == 0) it0 = atomicAdd(&ctrl->next_item, 1ull);
+        it0 = __shfl_sync(0xffffffffu, it0, 0);
+        const uint32_t p0 = it0 < nitems ? find_partition(a.item_prefix, a.P, it0) : 0u;
+        if (threadIdx.x == 0) {
+            s_next_item = it0;
+            s_next_part = p0;
         }
-        const uint32_t p = lo;
+    }
+    __syncthreads();
+
+    for (;;) {
+        const unsigned long long item = s_next_item;
+        const uint32_t p = s_next_part;
+        if (item >= nitems) break;
+        unsigned long long claim = 0;
+        if (threadIdx.x == 0) claim = atomicAdd(&ctrl->next_item, 1ull);
+
         const uint32_t bs0 = a.bstart[p], bsz = a.bstart[p + 1] - bs0;
         const uint32_t ps0 = a.pstart[p], psz = a.pstart[p + 1] - ps0;
         const uint32_t npc = (psz + kProbeChunk - 1) / kProbeChunk;
         const unsigned long long local = item - a.item_prefix[p];
         const uint32_t bc = (uint32_t)(local / npc), pc = (uint32_t)(local % npc);
-        const uint32_t b0 = bs0 + bc * kBuildCap;
         const uint32_t bn = bsz - bc * kBuildCap < kBuildCap ? bsz - bc * kBuildCap : kBuildCap;
-        const uint32_t p0 = ps0 + pc * kProbeChunk;
         const uint32_t pn = psz - pc * kProbeChunk < kProbeChunk ? psz - pc * kProbeChunk : kProbeChunk;
-        uint32_t tsize = 64;
-        while (tsize < 2 * bn) tsize <<= 1;
-        const uint32_t tmask = tsize - 1;
+        const KeyT* bkey = a.bkey + bs0 + bc * kBuildCap;
+        const uint32_t* bidx = a.bidx + bs0 + bc * kBuildCap;
+        const KeyT* pkey = a.pkey + ps0 + pc * kProbeChunk;
+        const uint32_t* pidx = a.pidx + ps0 + pc * kProbeChunk;
+        // about three slots per build row (load <= 1/3), at most kTableMax
+        uint32_t tsize = (3 * bn + 31) & ~31u;
+        if (tsize < 64) tsize = 64;
+        if (tsize > kTableMax) tsize = kTableMax;
 
-        for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) tab.clear(i);
+        // Issue the first build and probe loads before clearing the table, so
+        // their latency overlaps the clear.
+        RoundRegs<KeyT> cur, nxt;
+        load_round(nxt, bkey, bidx, 0, bn);
+        load_round(cur, pkey, pidx, 0, pn);
+        for (uint32_t i = threadIdx.x; i < tsize; i += kJoinThreads) tab.clear(i);
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < bn; i += blockDim.x) {
-            const KeyT k = a.bkey[b0 + i];
-            const uint32_t r = a.bidx[b0 + i];
-            uint32_t s = (uint32_t)KeyCodec<KeyT>::hash(k) & tmask;
-            for (uint32_t step = 0;; ++step) {
-                if (tab.insert(s, k, r)) break;
-                if (step == tmask) {
-                    atomicOr(&ctrl->err, kErrTableFull);
-                    break;
+        // Build. An insert that meets its own key proves a duplicate in this
+        // chunk; without one, every probe key has at most one match here.
+        int dup = sizeof(KeyT) != 4;  // 64-bit tables cannot see equal keys in flight
+        for (uint32_t bb = 0; bb < bn; bb += kRound) {
+            if (bb) load_round(nxt, bkey, bidx, bb, bn);
+#pragma unroll
+            for (int j = 0; j < kN; ++j) {
+                if (bb + j * kJoinThreads + threadIdx.x >= bn) continue;
+                uint32_t s = home_slot(nxt.k[j], tsize);
+                for (uint32_t step = 0;; ++step) {
+                    const int r = tab.insert(s, nxt.k[j], nxt.id[j]);
+                    if (r > 0) break;
+                    if (r < 0) dup = 1;
+                    if (step + 1 == tsize) {
+                        atomicOr(&ctrl->err, kErrTableFull);
+                        break;
+                    }
+                    s = next_slot(s, tsize);
                 }
-                s = (s + 1) & tmask;
             }
         }
-        __syncthreads();
+        const bool unique = __syncthreads_or(dup) == 0;
+        if (threadIdx.x < kWarp) {  // look up the next item while the probes run
+            claim = __shfl_sync(0xffffffffu, claim, 0);
+            const uint32_t pn2 = claim < nitems ? find_partition(a.item_prefix, a.P, claim) : 0u;
+            if (threadIdx.x == 0) {
+                s_next_item = claim;
+                s_next_part = pn2;
+            }
+        }
 
-        const uint32_t round = kJoinThreads * kJoinItems;
-        for (uint32_t base = 0; base < pn; base += round) {
-#pragma unroll 1
-            for (int it = 0; it < kJoinItems; ++it) {
-                const uint32_t i = base + it * kJoinThreads + threadIdx.x;
-                bool active = i < pn;
-                KeyT k = 0;
-                uint32_t id = 0, s = 0, steps = 0;
-                if (active) {
-                    k = __ldcs(a.pkey + p0 + i);
-                    id = __ldcs(a.pidx + p0 + i);
-                    s = (uint32_t)KeyCodec<KeyT>::hash(k) & tmask;
-                }
-                while (__any_sync(0xffffffffu, active)) {
-                    bool hit = false;
-                    uint32_t brow = 0;
-                    if (active) {
-                        const int r = tab.probe(s, k, brow);
-                        if (r == 0) {
-                            active = false;
-                        } else {
-                            hit = r == 2;
-                            s = (s + 1) & tmask;
-                            if (++steps > tmask) active = false;
+        for (uint32_t base = 0; base < pn; base += kRound) {
+            // the next round's loads are in flight while this round probes
+            if (base + kRound < pn) load_round(nxt, pkey, pidx, base + kRound, pn);
+            if (unique) {
+                // Fast path: stop at the first match, no collectives per step.
+#pragma unroll
+                for (int j = 0; j < kN; ++j) {
+                    uint32_t brow = kHole;
+                    if (base + j * kJoinThreads + threadIdx.x < pn) {
+                        const KeyT k = cur.k[j];
+                        uint32_t s = home_slot(k, tsize);
+                        for (uint32_t step = 0; step < tsize; ++step) {
+                            uint32_t r;
+                            const int q = tab.probe(s, k, r);
+                            if (q == 0) break;
+                            if (q == 2) {
+                                brow = r;
+                                break;
+                            }
+                            s = next_slot(s, tsize);
                         }
                     }
-                    emit<AGG, kJoinStage>(st, agg, hit, brow, id, out, ctrl);
+                    if (AGG) {
+                        if (brow != kHole) {
+                            agg.sum += (unsigned long long)read_pay(out.bpay, out.pay_bytes, brow) +
+                                       (unsigned long long)read_pay(out.ppay, out.pay_bytes, cur.id[j]);
+                            agg.count += 1;
+                        }
+                    } else {
+                        st.b[j * kJoinThreads + threadIdx.x] = brow;
+                        st.p[j * kJoinThreads + threadIdx.x] = cur.id[j];
+                    }
                 }
+                if (!AGG) flush_positional<kN>(st, s_grp, out, ctrl);
+            } else {
+                // General path (duplicate keys): every match of every chain,
+                // emitted through the warp-aggregated stage.
+#pragma unroll 1
+                for (int j = 0; j < kN; ++j) {
+                    bool active = base + j * kJoinThreads + threadIdx.x < pn;
+                    const KeyT k = cur.k[j];
+                    const uint32_t id = cur.id[j];
+                    uint32_t s = active ? home_slot(k, tsize) : 0u;
+                    uint32_t steps = 0;
+                    while (__any_sync(0xffffffffu, active)) {
+                        bool hit = false;
+                        uint32_t brow = 0;
+                        if (active) {
+                            const int r = tab.probe(s, k, brow);
+                            if (r == 0) {
+                                active = false;
+                            } else {
+                                hit = r == 2;
+                                s = next_slot(s, tsize);
+                                if (++steps == tsize) active = false;
+                            }
+                        }
+                        emit<AGG, kJoinStage>(st, agg, hit, brow, id, out, ctrl);
+                    }
+                }
+                stage_flush<AGG, kJoinStage>(st, out, ctrl);
             }
-            if (!AGG && stage_nearly_full(st, round)) stage_flush<AGG, kJoinStage>(st, out, ctrl);
+            cur = nxt;
         }
         __syncthreads();
     }
-    if (AGG)
-        agg_commit(agg, ctrl);
-    else
-        stage_flush<AGG, kJoinStage>(st, out, ctrl);
+    if (AGG) agg_commit(agg, ctrl);
 }
 
 template <typename KeyT>
@@ -310,14 +517,17 @@ cudaError_t phj_run(const JoinArgs& a, const PlanDev& plan, const PhjScratch& s,
     DevInfo di;
     cudaError_t e = current_device_info(&di);
     if (e != cudaSuccess) return e;
-    if ((e = partition_side(a.bkeys, a.nb, 0, plan, s.side[0], stream)) != cudaSuccess) return e;
-    if ((e = partition_side(a.pkeys, a.np, 1, plan, s.side[1], stream)) != cudaSuccess) return e;
+    if ((e = partition_side(a.bkeys, a.nb, 0, plan, s.side[0], &ctrl->err, stream)) != cudaSuccess)
+        return e;
+    if ((e = partition_side(a.pkeys, a.np, 1, plan, s.side[1], &ctrl->err, stream)) != cudaSuccess)
+        return e;
     const int passes = plan.variant == 3 ? 2 : 1;
     const uint32_t P = 1u << (plan.bits1 + (passes == 2 ? plan.bits2 : 0));
     {
-        ProfScope ps("phj_items", 24.0 * P, stream);
-        items_kernel<<<1, 1024, 0, stream>>>(s.side[0].part_start, s.side[1].part_start, P, s.item_prefix,
-                                             ctrl);
+        ProfScope ps("phj_items", 32.0 * P, stream, 0.0, 2);
+        items_count_kernel<<<(P + 255) / 256, 256, 0, stream>>>(s.side[0].part_start, s.side[1].part_start,
+                                                               P, s.item_prefix);
+        items_scan_kernel<<<1, 1024, 0, stream>>>(s.item_prefix, P, ctrl);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return plan.key32 ? launch_join<uint32_t>(s, plan, out, ctrl, di, stream, a.nb, a.np)
