@@ -30,8 +30,10 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
+    # EIGER_NVCC_FLAGS adds definitions for experiments (e.g. -DEIGER_JOIN_THREADS=256)
+    user = os.environ.get("EIGER_NVCC_FLAGS", "").split()
     return [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-            f"-I{os.path.dirname(HERE)}/include", *extra]
+            f"-I{os.path.dirname(HERE)}/include", *user, *extra]
 
 
 def build_library(verbose: bool = False, ptxas_verbose: bool = False) -> str:

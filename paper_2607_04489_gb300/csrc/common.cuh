@@ -6,6 +6,15 @@
 #include <stddef.h>
 #include <stdint.h>
 
+// Shape of the partitioned join: threads per CTA and build rows per
+// shared-memory table (the planner sizes partitions to half of that).
+#ifndef EIGER_JOIN_THREADS
+#define EIGER_JOIN_THREADS 512
+#endif
+#ifndef EIGER_BUILD_CAP
+#define EIGER_BUILD_CAP 4096
+#endif
+
 namespace eiger {
 
 // ---------------------------------------------------------------- constants

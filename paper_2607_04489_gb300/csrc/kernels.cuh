@@ -82,7 +82,10 @@ cudaError_t nphj_run(const JoinArgs& a, const PlanDev& plan, const NphjScratch& 
 
 // ------------------------------------------------------------------ PHJ
 
-constexpr int kPartTile = 4096;  // rows per partitioning tile
+#ifndef EIGER_PART_TILE
+#define EIGER_PART_TILE 4096
+#endif
+constexpr int kPartTile = EIGER_PART_TILE;  // rows per partitioning tile
 constexpr int kMaxBits = 12;     // radix bits per pass
 
 struct Tile {

@@ -28,8 +28,11 @@ namespace eiger {
 
 namespace {
 
-constexpr int kPartThreads = 512;
-constexpr int kPartItems = kPartTile / kPartThreads;  // 8 rows per thread
+#ifndef EIGER_PART_THREADS
+#define EIGER_PART_THREADS 512
+#endif
+constexpr int kPartThreads = EIGER_PART_THREADS;
+constexpr int kPartItems = kPartTile / kPartThreads;  // rows per thread per tile
 constexpr uint32_t kNoDigit = 0xFFFFFFFFu;
 
 constexpr int kScanThreads = 512;
@@ -288,9 +291,12 @@ __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey,
 template <typename InKey, typename KeyT, bool FIRST>
 __host__ __device__ constexpr size_t scatter_smem_bytes(int bits) {
     return align_up(16 + 3 * ((size_t)1 << bits) * sizeof(uint32_t), 16) +
-           2 * PassIn<InKey, KeyT, FIRST>::kBufBytes +
-           align_up((size_t)kPartTile * sizeof(KeyT), 16) + (size_t)kPartTile * sizeof(uint32_t);
+           2 * PassIn<InKey, KeyT, FIRST>::kBufBytes + align_up((size_t)kPartTile * sizeof(KeyT), 16) +
+           (size_t)kPartTile * sizeof(uint32_t) + (size_t)kPartTile * sizeof(uint16_t);
 }
+
+// Digits a thread owns in the per-tile offset table (prefetched one tile ahead).
+constexpr int kGoffPerThread = (1 << kMaxBits) / kPartThreads;
 
 template <typename InKey, typename KeyT, bool FIRST>
 __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InKey, KeyT> a, unsigned* err) {
@@ -308,33 +314,59 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
     KeyT* s_key = reinterpret_cast<KeyT*>(smem + ring_off + 2 * P::kBufBytes);
     uint32_t* s_idx = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(s_key) +
                                                   align_up((size_t)kPartTile * sizeof(KeyT), 16));
+    uint16_t* s_dig = reinterpret_cast<uint16_t*>(s_idx + kPartTile);
     __syncthreads();
 
     const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
     uint32_t t = blockIdx.x;
+    // Global offsets of this CTA's first tile; later ones are loaded one tile
+    // ahead into registers (thread i owns digits i, i + blockDim, ...).
+    uint32_t goff[kGoffPerThread];
+    Tile tl_cur;
+    if (t < ntiles) {
+        tl_cur = get_tile(a, t);
+#pragma unroll
+        for (int q = 0; q < kGoffPerThread; ++q) {
+            const uint32_t d = threadIdx.x + q * kPartThreads;
+            goff[q] = d < nd ? a.counts[count_index(tl_cur, t, d, a.bits)] : 0u;
+        }
+    }
     if (threadIdx.x < kWarp && t < ntiles) ring.issue(a, t, 0);
     for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
         const int b = it & 1;
         const uint32_t tn = t + gridDim.x;
         if (threadIdx.x < kWarp && tn < ntiles) ring.issue(a, tn, b ^ 1);
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
+#pragma unroll
+        for (int q = 0; q < kGoffPerThread; ++q) {
+            const uint32_t d = threadIdx.x + q * kPartThreads;
+            if (d < nd) s_goff[d] = goff[q];
+        }
         const bool ok = mbar_wait(&ring.bar[b], (it >> 1) & 1);
         if (__syncthreads_or(!ok)) {
             ring_abort(ring, b ^ 1, ((it + 1) >> 1) & 1, tn < ntiles, err);
             return;
         }
-        const Tile tl = get_tile(a, t);
+        const Tile tl = tl_cur;
+        if (tn < ntiles) {  // next tile's offsets, consumed next iteration
+            tl_cur = get_tile(a, tn);
+#pragma unroll
+            for (int q = 0; q < kGoffPerThread; ++q) {
+                const uint32_t d = threadIdx.x + q * kPartThreads;
+                goff[q] = d < nd ? a.counts[count_index(tl_cur, tn, d, a.bits)] : 0u;
+            }
+        }
         const auto* kbuf = ring.keys(b) + lead_of(Ring::key_src(a, tl.start));
         const uint32_t* rbuf = nullptr;
         if constexpr (!FIRST) rbuf = ring.rows(b) + lead_of(a.in_idx + tl.start);
 
+        KeyT kk[kPartItems];
         uint32_t dr[kPartItems];  // (rank << 12) | digit, or kNoDigit
 #pragma unroll
         for (int j = 0; j < kPartItems; ++j) {
             const uint32_t e = j * kPartThreads + threadIdx.x;
             dr[j] = kNoDigit;
-            KeyT k;
-            if (e < tl.len && tile_key<InKey, KeyT, FIRST>(a, kbuf, e, k)) dr[j] = digit_of(k, a.dshift, a.dmask);
+            if (e < tl.len && tile_key<InKey, KeyT, FIRST>(a, kbuf, e, kk[j])) dr[j] = digit_of(kk[j], a.dshift, a.dmask);
         }
 #pragma unroll
         for (int j = 0; j < kPartItems; ++j)
@@ -342,8 +374,6 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
         __syncthreads();
 
         const uint32_t kept = block_scan_smem(s_cnt, s_start, nd, s_warp);
-        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x)
-            s_goff[d] = s_cnt[d] ? a.counts[count_index(tl, t, d, a.bits)] : 0u;
         if (threadIdx.x == 0) s_kept = kept;
         __syncthreads();
 
@@ -351,10 +381,10 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
         for (int j = 0; j < kPartItems; ++j) {
             if (dr[j] != kNoDigit) {
                 const uint32_t e = j * kPartThreads + threadIdx.x;
-                const uint32_t pos = s_start[dr[j] & 0xFFFu] + (dr[j] >> 12);
-                KeyT k;
-                tile_key<InKey, KeyT, FIRST>(a, kbuf, e, k);
-                s_key[pos] = k;
+                const uint32_t d = dr[j] & 0xFFFu;
+                const uint32_t pos = s_start[d] + (dr[j] >> 12);
+                s_key[pos] = kk[j];
+                s_dig[pos] = (uint16_t)d;
                 if constexpr (FIRST)
                     s_idx[pos] = tl.start + e;
                 else
@@ -365,10 +395,9 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
 
         const uint32_t nk = s_kept;
         for (uint32_t pos = threadIdx.x; pos < nk; pos += blockDim.x) {
-            const KeyT k = s_key[pos];
-            const uint32_t d = digit_of(k, a.dshift, a.dmask);
+            const uint32_t d = s_dig[pos];
             const uint32_t g = s_goff[d] + (pos - s_start[d]);
-            a.out_key[g] = k;
+            a.out_key[g] = s_key[pos];
             a.out_idx[g] = s_idx[pos];
         }
         __syncthreads();

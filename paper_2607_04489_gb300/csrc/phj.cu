@@ -25,10 +25,11 @@ size_t part_scan_blocks(size_t counts_len);
 
 namespace {
 
-constexpr int kJoinThreads = 512;
+constexpr int kJoinThreads = EIGER_JOIN_THREADS;
+constexpr int kJoinMinBlocks = 1024 / kJoinThreads;  // 64 registers per thread
 constexpr int kMaxRows = 8;                       // rows per thread per round (32-bit keys)
 constexpr int kJoinStage = kJoinThreads * kMaxRows;  // a unique-key round never spills
-constexpr uint32_t kBuildCap = 4096;              // build rows per shared-memory table
+constexpr uint32_t kBuildCap = EIGER_BUILD_CAP;   // build rows per shared-memory table
 
 // Rows each thread keeps in flight per round: 8 for 32-bit keys, 4 for 64-bit
 // keys (register budget of two 512-thread CTAs per SM).
@@ -126,10 +127,13 @@ struct SmemTable;
 // the top bits of the hash, so the hash is first remixed by an odd multiplier
 // (which carries its low bits into the high bits) and then mapped onto
 // [0, tsize) by a multiply-shift range reduction.
+// Slots come in aligned pairs: the home slot is even, so a probe reads its
+// first two candidates with one 16-byte shared load (inserts are ordinary
+// linear probing from the same home slot, filling a pair's first slot first).
 template <typename KeyT>
 __device__ __forceinline__ uint32_t home_slot(KeyT k, uint32_t tsize) {
     const uint32_t h = (uint32_t)KeyCodec<KeyT>::hash(k) * 0x9E3779B1u;
-    return (uint32_t)(((unsigned long long)h * tsize) >> 32);
+    return 2u * (uint32_t)(((unsigned long long)h * (tsize >> 1)) >> 32);
 }
 
 __device__ __forceinline__ uint32_t next_slot(uint32_t s, uint32_t tsize) {
@@ -149,6 +153,8 @@ struct SmemTable<uint32_t> {
         if (prev == kEmptySlot) return 1;
         return (uint32_t)(prev >> 32) == k ? -1 : 0;
     }
+    // the aligned pair of slots starting at even slot s
+    __device__ ulonglong2 pair(uint32_t s) const { return *reinterpret_cast<const ulonglong2*>(slot + s); }
     // 0: empty (chain ends), 1: occupied, other key, 2: match
     __device__ int probe(uint32_t s, uint32_t k, uint32_t& row) const {
         const unsigned long long v = slot[s];
@@ -233,7 +239,7 @@ constexpr int kJoinWarps = kJoinThreads / kWarp;
 // rank within its (row j, warp) group, one scan over the kN x warps group
 // counts places the groups, one global atomic reserves the round's output,
 // and each warp then writes its group to consecutive output positions.
-template <int kN>
+template <int kN, bool PAIRS>
 __device__ __forceinline__ void flush_positional(Stage<kJoinStage>& st, uint32_t* s_grp,
                                                  const JoinOut& out, Ctrl* ctrl) {
     const unsigned lane = lane_id();
@@ -270,22 +276,34 @@ __device__ __forceinline__ void flush_positional(Stage<kJoinStage>& st, uint32_t
             run += v[i];
         }
         const uint32_t total = __shfl_sync(0xffffffffu, x, kWarp - 1);
-        if (lane == 0) st.base = total ? atomicAdd(&ctrl->cursor, (unsigned long long)total) : 0ull;
+        if (lane == 0) {
+            st.base = total ? atomicAdd(&ctrl->cursor, (unsigned long long)total) : 0ull;
+            st.count = (unsigned)(st.base + total <= out.capacity);  // whole round fits
+        }
     }
     __syncthreads();
     const unsigned long long base = st.base;
+    const bool fits = st.count != 0;
     const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < kN; ++j) {
         const uint32_t i = j * kJoinThreads + threadIdx.x;
-        if (ball[j] & (1u << lane))
-            write_match(out, base + s_grp[j * kJoinWarps + w] + __popc(ball[j] & lt), st.b[i], st.p[i]);
+        if (ball[j] & (1u << lane)) {
+            const unsigned long long pos = base + s_grp[j * kJoinWarps + w] + __popc(ball[j] & lt);
+            if (PAIRS && fits) {
+                out.bidx[pos] = st.b[i];
+                out.pidx[pos] = st.p[i];
+            } else {
+                write_match(out, pos, st.b[i], st.p[i]);
+            }
+        }
     }
     __syncthreads();
+    if (threadIdx.x == 0) st.count = 0;
 }
 
-template <typename KeyT, bool AGG>
-__global__ void __launch_bounds__(kJoinThreads, 2)
+template <typename KeyT, bool AGG, bool PAIRS>
+__global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
     phj_join_kernel(JoinIn<KeyT> a, JoinOut out, Ctrl* ctrl) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Stage<kJoinStage> st;
@@ -387,15 +405,32 @@ __global__ void __launch_bounds__(kJoinThreads, 2)
                     if (base + j * kJoinThreads + threadIdx.x < pn) {
                         const KeyT k = cur.k[j];
                         uint32_t s = home_slot(k, tsize);
-                        for (uint32_t step = 0; step < tsize; ++step) {
-                            uint32_t r;
-                            const int q = tab.probe(s, k, r);
-                            if (q == 0) break;
-                            if (q == 2) {
-                                brow = r;
-                                break;
+                        if constexpr (sizeof(KeyT) == 4) {
+                            for (uint32_t step = 0; step < tsize; step += 2) {
+                                const ulonglong2 v = tab.pair(s);
+                                if (v.x == kEmptySlot) break;
+                                if ((uint32_t)(v.x >> 32) == (uint32_t)k) {
+                                    brow = (uint32_t)v.x;
+                                    break;
+                                }
+                                if (v.y == kEmptySlot) break;
+                                if ((uint32_t)(v.y >> 32) == (uint32_t)k) {
+                                    brow = (uint32_t)v.y;
+                                    break;
+                                }
+                                s = s + 2 == tsize ? 0u : s + 2;
                             }
-                            s = next_slot(s, tsize);
+                        } else {
+                            for (uint32_t step = 0; step < tsize; ++step) {
+                                uint32_t r;
+                                const int q = tab.probe(s, k, r);
+                                if (q == 0) break;
+                                if (q == 2) {
+                                    brow = r;
+                                    break;
+                                }
+                                s = next_slot(s, tsize);
+                            }
                         }
                     }
                     if (AGG) {
@@ -409,7 +444,7 @@ __global__ void __launch_bounds__(kJoinThreads, 2)
                         st.p[j * kJoinThreads + threadIdx.x] = cur.id[j];
                     }
                 }
-                if (!AGG) flush_positional<kN>(st, s_grp, out, ctrl);
+                if (!AGG) flush_positional<kN, PAIRS>(st, s_grp, out, ctrl);
             } else {
                 // General path (duplicate keys): every match of every chain,
                 // emitted through the warp-aggregated stage.
@@ -464,7 +499,10 @@ cudaError_t launch_join(const PhjScratch& s, const PlanDev& plan, const JoinOut&
     a.pstart = s.side[1].part_start;
     a.item_prefix = s.item_prefix;
     a.P = 1u << (plan.bits1 + (passes == 2 ? plan.bits2 : 0));
-    auto kern = out.aggregate ? phj_join_kernel<KeyT, true> : phj_join_kernel<KeyT, false>;
+    const bool pairs = !out.aggregate && out.bidx && out.pidx && !out.bpay_out && !out.ppay_out;
+    auto kern = out.aggregate ? phj_join_kernel<KeyT, true, false>
+                : pairs       ? phj_join_kernel<KeyT, false, true>
+                              : phj_join_kernel<KeyT, false, false>;
     // reads every partitioned (key', row) of both sides once, writes the matches
     const double tuple = (double)(sizeof(KeyT) + sizeof(uint32_t));
     ProfScope ps("phj_join", tuple * (double)(nb + np), stream, match_bytes(out));

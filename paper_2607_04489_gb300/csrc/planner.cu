@@ -16,12 +16,13 @@
 #include <algorithm>
 #include <cmath>
 
+#include "common.cuh"
 #include "planner.h"
 
 namespace eiger {
 
 namespace {
-constexpr int64_t kTargetRows = 2048;  // average build rows per partition
+constexpr int64_t kTargetRows = EIGER_BUILD_CAP / 2;  // average build rows per partition
 constexpr int kOnePassBits = 8;
 constexpr int kMaxTotalBits = 20;
 }  // namespace
