@@ -84,6 +84,38 @@ def barrier(world: int):
         dist.barrier()
 
 
+def kernel_sources_digest() -> str:
+    """Digest of the CUDA sources, to tell whether recorded ncu counters still
+    describe the kernels that run."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2607_04489_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                   glob.glob(os.path.join(csrc, "*.h")))
+    for p in files:
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from profiles/dram_traffic.txt, or None
+    when the file is missing or was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        with open(path) as f:
+            rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    except OSError:
+        return None
+    table = {r[0]: r[1] for r in rows if len(r) == 2}
+    if table.get("sources") != kernel_sources_digest() or kernel not in table:
+        return None
+    return float(table[kernel])
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -164,7 +196,7 @@ def workload_desc(args):
             f"output (build_idx, probe_idx) pairs"), nb, nb * args.ratio
 
 
-def cpu_oracle_sample(args, min_seconds=10.0):
+def cpu_oracle_sample(args, min_seconds=12.0):
     """The oracle, as it stands, on a bounded sample of the workload."""
     import oracle
     from paper_2607_04489_gb300 import workloads
@@ -178,7 +210,7 @@ def cpu_oracle_sample(args, min_seconds=10.0):
         oracle.join(bk, pk)
         runs += 1
         el = time.perf_counter() - t0
-        if el >= min_seconds or runs >= 8:
+        if el >= min_seconds or runs >= 64:
             break
     tput = runs * (bk.size + pk.size) / el
     return {"value": tput, "unit": "tuples/s", "cores": 1, "kind": "oracle",
@@ -364,7 +396,7 @@ def run_eiger(args):
                  "narrow": plan.narrow, "load_factor": plan.load_factor},
         "roofline": {"bound": "hbm", "kernel": dom["stage"], "achieved": dom["gbs"], "peak": hbm,
                      "peak_source": peak_src, "unit": "GB/s", "frac": dom["gbs"] / hbm,
-                     "traffic": None},
+                     "traffic": recorded_traffic(dom["stage"]), "algorithmic_bytes": dom["bytes"]},
         "stages": stage_rows,
         "gpu_launches": launches,
         "static": static,
