@@ -183,6 +183,54 @@ eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* 
                             int64_t* out_sum, int64_t* out_count, void* d_workspace,
                             size_t ws_bytes, eiger_plan_t* plan_used, void* stream);
 
+/* One join of a batch (eiger_join_batched). All pointers are device memory. */
+typedef struct {
+    const void* build_keys;  /* nb keys of the batch's dtype                 */
+    const void* probe_keys;  /* np keys                                      */
+    int64_t nb;
+    int64_t np;
+    uint32_t* out_bidx;      /* capacity entries, or NULL                     */
+    uint32_t* out_pidx;      /* capacity entries, or NULL                     */
+    int64_t capacity;
+} eiger_join_desc;
+
+/* Launch shape of the batched join, chosen by the autotuner. */
+typedef struct {
+    int32_t block_threads;   /* 128, 256 or 512                               */
+    int32_t chunk_rows;      /* rows per work item: 4096, 16384 or 65536      */
+    float load_factor;       /* per-join table load, in (0, 0.9]               */
+} eiger_batch_knobs;
+
+/*
+ * Scratch bytes eiger_join_batched needs for these joins (host copy of the
+ * descriptors; only nb, np are read). knobs NULL = defaults.
+ * Errors: INVALID_ARG.
+ */
+eiger_status eiger_join_batched_workspace(const eiger_join_desc* h_descs, int32_t k, eiger_dtype dtype,
+                                          const eiger_batch_knobs* knobs, size_t* bytes);
+
+/*
+ * eiger_join_batched -- k independent equi-joins (Sec. 3.2) in one persistent
+ * launch. Each join gets its own global open-addressing multiset in the
+ * workspace (no statistics: the batch targets many small joins whose tables
+ * fit the L2 cache, Sec. 5.2.2 "medium and small joins"); work items are
+ * build chunks and probe chunks of every join, interleaved per join and pulled
+ * by a persistent grid, a probe chunk waiting (bounded) until its join's build
+ * chunks are in. Join j's matches go to its own outputs in unspecified order;
+ * d_counts[j] receives |J_j| (entries beyond capacity are not written).
+ * d_descs: k descriptors in device memory. d_counts: k int64, device.
+ * d_status: one int32, device: 0 on success, else an eiger_status value
+ * (EIGER_ERR_TABLE_FULL, EIGER_ERR_INTERNAL, EIGER_ERR_WORKSPACE).
+ * Nothing is synchronised or copied to the host, so the call can be captured
+ * in a CUDA graph and replayed; the descriptors and workspace must then stay
+ * valid. Host-side errors: INVALID_ARG (bad k, dtype, knobs, NULL pointers),
+ * CUDA.
+ */
+eiger_status eiger_join_batched(eiger_dtype dtype, const eiger_join_desc* d_descs, int32_t k,
+                                int64_t* d_counts, int32_t* d_status,
+                                const eiger_batch_knobs* knobs, void* d_workspace, size_t ws_bytes,
+                                void* stream);
+
 /*
  * eiger_join_static_noalloc -- the static non-partitioned join for callers that
  * cannot allocate device memory. The paper has no counterpart; this entry

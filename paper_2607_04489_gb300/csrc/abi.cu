@@ -472,6 +472,77 @@ eiger_status eiger_join(eiger_dtype dtype, const void* d_bkeys, const void* d_bp
     return run_join(c);
 }
 
+namespace {
+
+eiger_batch_knobs batch_defaults() {
+    eiger_batch_knobs k;
+    k.block_threads = 256;
+    k.chunk_rows = 16384;
+    k.load_factor = 0.5f;
+    return k;
+}
+
+eiger_status check_batch_knobs(const eiger_batch_knobs& k) {
+    if (k.block_threads != 128 && k.block_threads != 256 && k.block_threads != 512)
+        return fail(EIGER_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
+    if (k.chunk_rows < 1024 || k.chunk_rows > (1 << 20))
+        return fail(EIGER_ERR_INVALID_ARG, "chunk_rows must be in [1024, 2^20]");
+    if (!(k.load_factor > 0.0f && k.load_factor <= 0.9f))
+        return fail(EIGER_ERR_INVALID_ARG, "load_factor outside (0, 0.9]");
+    return EIGER_OK;
+}
+
+}  // namespace
+
+extern "C" eiger_status eiger_join_batched_workspace(const eiger_join_desc* h_descs, int32_t k,
+                                                     eiger_dtype dtype, const eiger_batch_knobs* knobs,
+                                                     size_t* bytes) {
+    if (!bytes) return fail(EIGER_ERR_INVALID_ARG, "bytes is NULL");
+    if (k < 0 || (k > 0 && !h_descs)) return fail(EIGER_ERR_INVALID_ARG, "bad descriptor list");
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
+    const eiger_batch_knobs kn = knobs ? *knobs : batch_defaults();
+    eiger_status s = check_batch_knobs(kn);
+    if (s != EIGER_OK) return s;
+    unsigned long long slots = 0;
+    for (int j = 0; j < k; ++j) {
+        const int64_t nb = h_descs[j].nb, np = h_descs[j].np;
+        if (nb < 0 || np < 0 || nb > kMaxRows || np > kMaxRows)
+            return fail(EIGER_ERR_INVALID_ARG, "join %d: row counts must be in [0, 2^32)", j);
+        if (nb > 0 && np > 0) slots += table_slots(nb, (double)kn.load_factor);
+    }
+    Carve c{nullptr, 0};
+    batch_layout(c, k, slots, dtype == EIGER_I32 ? 8 : 16);
+    *bytes = c.off;
+    return EIGER_OK;
+}
+
+extern "C" eiger_status eiger_join_batched(eiger_dtype dtype, const eiger_join_desc* d_descs, int32_t k,
+                                           int64_t* d_counts, int32_t* d_status,
+                                           const eiger_batch_knobs* knobs, void* d_workspace,
+                                           size_t ws_bytes, void* stream) {
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
+    if (k < 0) return fail(EIGER_ERR_INVALID_ARG, "k < 0");
+    if (!d_status) return fail(EIGER_ERR_INVALID_ARG, "d_status is NULL");
+    if (k > 0 && (!d_descs || !d_counts || !d_workspace))
+        return fail(EIGER_ERR_INVALID_ARG, "NULL descriptors, counts or workspace");
+    const eiger_batch_knobs kn = knobs ? *knobs : batch_defaults();
+    eiger_status s = check_batch_knobs(kn);
+    if (s != EIGER_OK) return s;
+    const int slot_bytes = dtype == EIGER_I32 ? 8 : 16;
+    Carve probe{nullptr, 0};
+    batch_layout(probe, k, 0, slot_bytes);
+    if (probe.off > ws_bytes) return fail(EIGER_ERR_WORKSPACE, "workspace smaller than the batch bookkeeping");
+    // whatever follows the bookkeeping holds the tables
+    const unsigned long long cap_slots = (ws_bytes - probe.off) / (size_t)slot_bytes;
+    Carve c{static_cast<char*>(d_workspace), 0};
+    const BatchLayout L = batch_layout(c, k, cap_slots, slot_bytes);
+    if (k == 0) return EIGER_OK;
+    EIGER_CUDA(batch_run(d_descs, k, dtype, kn, L, reinterpret_cast<long long*>(d_counts), d_status,
+                         static_cast<cudaStream_t>(stream)),
+               "batched join");
+    return EIGER_OK;
+}
+
 eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* d_bpay, int64_t nb,
                             const void* d_pkeys, const void* d_ppay, int64_t np, int32_t payload_bytes,
                             eiger_variant variant, const eiger_plan_t* knobs, int64_t* out_sum,

@@ -42,7 +42,7 @@ struct AggState {
 // Warp-collective: all 32 lanes call it; lanes with `has` emit the pair (b, p).
 template <bool AGG, int STAGE>
 __device__ __forceinline__ void emit(Stage<STAGE>& st, AggState& agg, bool has, uint32_t b,
-                                     uint32_t p, const JoinOut& out, Ctrl* ctrl) {
+                                     uint32_t p, const JoinOut& out, unsigned long long* cursor) {
     if (AGG) {
         if (has) {
             agg.sum += (unsigned long long)read_pay(out.bpay, out.pay_bytes, b) +
@@ -68,7 +68,7 @@ __device__ __forceinline__ void emit(Stage<STAGE>& st, AggState& agg, bool has, 
     if (smask) {
         const int sl = __ffs(smask) - 1;
         unsigned long long g0 = 0;
-        if ((int)lane == sl) g0 = atomicAdd(&ctrl->cursor, (unsigned long long)__popc(smask));
+        if ((int)lane == sl) g0 = atomicAdd(cursor, (unsigned long long)__popc(smask));
         g0 = __shfl_sync(0xffffffffu, g0, sl);
         if (spill) write_match(out, g0 + __popc(smask & lanemask_lt()), b, p);
     }
@@ -76,11 +76,11 @@ __device__ __forceinline__ void emit(Stage<STAGE>& st, AggState& agg, bool has, 
 
 // Block-collective: writes the staged matches out and empties the stage.
 template <bool AGG, int STAGE>
-__device__ __forceinline__ void stage_flush(Stage<STAGE>& st, const JoinOut& out, Ctrl* ctrl) {
+__device__ __forceinline__ void stage_flush(Stage<STAGE>& st, const JoinOut& out, unsigned long long* cursor) {
     if (AGG) return;
     __syncthreads();
     const unsigned n = st.count < (unsigned)STAGE ? st.count : (unsigned)STAGE;
-    if (threadIdx.x == 0) st.base = n ? atomicAdd(&ctrl->cursor, (unsigned long long)n) : 0ull;
+    if (threadIdx.x == 0) st.base = n ? atomicAdd(cursor, (unsigned long long)n) : 0ull;
     __syncthreads();
     const unsigned long long base = st.base;
     for (unsigned i = threadIdx.x; i < n; i += blockDim.x) write_match(out, base + i, st.b[i], st.p[i]);

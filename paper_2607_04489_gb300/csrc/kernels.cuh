@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "eiger.h"
 
 namespace eiger {
 
@@ -122,5 +123,20 @@ cudaError_t partition_side(const void* keys, int64_t n, int side, const PlanDev&
                            const PartSide& s, unsigned* err, cudaStream_t stream);
 cudaError_t phj_run(const JoinArgs& a, const PlanDev& plan, const PhjScratch& s, const JoinOut& out,
                     Ctrl* ctrl, cudaStream_t stream);
+
+// ------------------------------------------------------------------ batches
+
+struct BatchLayout {
+    unsigned char* ctrl;
+    unsigned char* meta;
+    unsigned long long* item_prefix;  // [k + 1]
+    unsigned* built;                  // [k]
+    unsigned char* tables;
+    unsigned long long table_slots;   // capacity of `tables` in slots
+};
+
+BatchLayout batch_layout(Carve& c, int k, unsigned long long total_slots, int slot_bytes);
+cudaError_t batch_run(const eiger_join_desc* d_descs, int k, int dtype, const eiger_batch_knobs& knobs,
+                      const BatchLayout& L, long long* d_counts, int* d_status, cudaStream_t stream);
 
 }  // namespace eiger

@@ -110,15 +110,15 @@ __global__ void __launch_bounds__(kProbeThreads)
                         }
                     }
                 }
-                emit<AGG, kStage>(st, agg, hit, bi, (uint32_t)r, out, ctrl);
+                emit<AGG, kStage>(st, agg, hit, bi, (uint32_t)r, out, &ctrl->cursor);
             }
         }
-        if (!AGG && stage_nearly_full(st, (unsigned)round)) stage_flush<AGG, kStage>(st, out, ctrl);
+        if (!AGG && stage_nearly_full(st, (unsigned)round)) stage_flush<AGG, kStage>(st, out, &ctrl->cursor);
     }
     if (AGG)
         agg_commit(agg, ctrl);
     else
-        stage_flush<AGG, kStage>(st, out, ctrl);
+        stage_flush<AGG, kStage>(st, out, &ctrl->cursor);
 }
 
 template <bool AGG>
@@ -163,15 +163,15 @@ __global__ void __launch_bounds__(kProbeThreads)
                         }
                     }
                 }
-                emit<AGG, kStage>(st, agg, hit, bi, (uint32_t)r, out, ctrl);
+                emit<AGG, kStage>(st, agg, hit, bi, (uint32_t)r, out, &ctrl->cursor);
             }
         }
-        if (!AGG && stage_nearly_full(st, (unsigned)round)) stage_flush<AGG, kStage>(st, out, ctrl);
+        if (!AGG && stage_nearly_full(st, (unsigned)round)) stage_flush<AGG, kStage>(st, out, &ctrl->cursor);
     }
     if (AGG)
         agg_commit(agg, ctrl);
     else
-        stage_flush<AGG, kStage>(st, out, ctrl);
+        stage_flush<AGG, kStage>(st, out, &ctrl->cursor);
 }
 
 template <typename Kern>

@@ -468,10 +468,10 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
                                 if (++steps == tsize) active = false;
                             }
                         }
-                        emit<AGG, kJoinStage>(st, agg, hit, brow, id, out, ctrl);
+                        emit<AGG, kJoinStage>(st, agg, hit, brow, id, out, &ctrl->cursor);
                     }
                 }
-                stage_flush<AGG, kJoinStage>(st, out, ctrl);
+                stage_flush<AGG, kJoinStage>(st, out, &ctrl->cursor);
             }
             cur = nxt;
         }

@@ -54,6 +54,17 @@ class StageT(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
+class JoinDescT(ctypes.Structure):
+    _fields_ = [("build_keys", ctypes.c_void_p), ("probe_keys", ctypes.c_void_p), ("nb", ctypes.c_int64),
+                ("np", ctypes.c_int64), ("out_bidx", ctypes.c_void_p), ("out_pidx", ctypes.c_void_p),
+                ("capacity", ctypes.c_int64)]
+
+
+class BatchKnobsT(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("chunk_rows", ctypes.c_int32),
+                ("load_factor", ctypes.c_float)]
+
+
 class PlanT(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("bits1", ctypes.c_int32), ("bits2", ctypes.c_int32),
                 ("narrow", ctypes.c_int32), ("load_factor", ctypes.c_float),
@@ -108,8 +119,9 @@ _lib = None
 
 # Every symbol include/eiger.h declares (checked against the header by the tests).
 SYMBOLS = ("eiger_stats_workspace", "eiger_stats", "eiger_plan", "eiger_join_workspace", "eiger_join",
-           "eiger_join_sum", "eiger_join_static_noalloc", "eiger_profile", "eiger_profile_read",
-           "eiger_last_error", "eiger_version")
+           "eiger_join_sum", "eiger_join_batched_workspace", "eiger_join_batched",
+           "eiger_join_static_noalloc", "eiger_profile", "eiger_profile_read", "eiger_last_error",
+           "eiger_version")
 
 
 def load():
@@ -142,6 +154,11 @@ def load():
     lib.eiger_join_sum.argtypes = [c.c_int, vp, vp, i64, vp, vp, i64, i32, c.c_int,
                                    c.POINTER(PlanT), c.POINTER(i64), c.POINTER(i64), vp, sz,
                                    c.POINTER(PlanT), vp]
+    lib.eiger_join_batched_workspace.restype = c.c_int
+    lib.eiger_join_batched_workspace.argtypes = [c.POINTER(JoinDescT), c.c_int32, c.c_int,
+                                                 c.POINTER(BatchKnobsT), c.POINTER(sz)]
+    lib.eiger_join_batched.restype = c.c_int
+    lib.eiger_join_batched.argtypes = [c.c_int, vp, c.c_int32, vp, vp, c.POINTER(BatchKnobsT), vp, sz, vp]
     lib.eiger_join_static_noalloc.restype = c.c_int
     lib.eiger_join_static_noalloc.argtypes = [c.c_int, vp, i64, vp, i64, vp, vp, i64, c.POINTER(i64),
                                               vp]
@@ -353,3 +370,108 @@ def join_static_noalloc_into(build_keys, probe_keys, out_bidx, out_pidx, capacit
                                        probe_keys.numel(), _ptr(out_bidx), _ptr(out_pidx), capacity,
                                        ctypes.byref(cnt), _stream(stream))
     return st, cnt.value
+
+
+@dataclass
+class BatchKnobs:
+    block_threads: int = 256
+    chunk_rows: int = 16384
+    load_factor: float = 0.5
+
+    def to_c(self) -> BatchKnobsT:
+        return BatchKnobsT(self.block_threads, self.chunk_rows, self.load_factor)
+
+
+class BatchedJoin:
+    """k independent joins run by one eiger_join_batched call.
+
+    Build and probe key columns are given as lists of device tensors (one
+    dtype). Outputs live in two concatenated uint32 buffers; join j's pairs are
+    out_bidx[off[j] : off[j] + counts[j]] (capped at its capacity). ``run``
+    enqueues the call on the current stream; ``capture`` records it into a CUDA
+    graph whose replays redo the whole batch.
+    """
+
+    def __init__(self, builds, probes, capacities=None, knobs: "BatchKnobs | None" = None):
+        if len(builds) != len(probes):
+            raise ValueError("builds and probes differ in length")
+        lib = load()
+        self.k = len(builds)
+        self.builds = [b.contiguous() for b in builds]
+        self.probes = [p.contiguous() for p in probes]
+        dts = {_dtype_code(t) for t in self.builds + self.probes} or {I32}
+        if len(dts) != 1:
+            raise TypeError("all key columns of a batch must share one dtype")
+        self.dtype = dts.pop()
+        dev = torch.device("cuda")
+        caps = [p.numel() for p in self.probes] if capacities is None else list(capacities)
+        self.capacities = caps
+        self.off = np.zeros(self.k + 1, np.int64)
+        self.off[1:] = np.cumsum(caps)
+        total = int(self.off[-1])
+        self.out_bidx = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+        self.out_pidx = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+        descs = (JoinDescT * max(self.k, 1))()
+        for j in range(self.k):
+            d = descs[j]
+            d.build_keys = self.builds[j].data_ptr() if self.builds[j].numel() else None
+            d.probe_keys = self.probes[j].data_ptr() if self.probes[j].numel() else None
+            d.nb, d.np = self.builds[j].numel(), self.probes[j].numel()
+            d.out_bidx = self.out_bidx.data_ptr() + 4 * int(self.off[j])
+            d.out_pidx = self.out_pidx.data_ptr() + 4 * int(self.off[j])
+            d.capacity = int(caps[j])
+        self.knobs = knobs if knobs is not None else (load_tuned_batch_knobs() or BatchKnobs())
+        kc = self.knobs.to_c()
+        ws = ctypes.c_size_t(0)
+        _check(lib.eiger_join_batched_workspace(descs, self.k, self.dtype, ctypes.byref(kc),
+                                                ctypes.byref(ws)))
+        self.workspace = torch.empty(max(ws.value, 1), dtype=torch.uint8, device=dev)
+        raw = bytes(descs)[: ctypes.sizeof(JoinDescT) * self.k]
+        self.d_descs = torch.frombuffer(bytearray(raw or b"\0"), dtype=torch.uint8).to(dev)
+        self.counts = torch.zeros(max(self.k, 1), dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self._kc = kc
+
+    def run(self, stream=None):
+        _check(load().eiger_join_batched(self.dtype, _ptr(self.d_descs), self.k, _ptr(self.counts),
+                                         _ptr(self.status), ctypes.byref(self._kc), _ptr(self.workspace),
+                                         self.workspace.numel(), _stream(stream)))
+
+    def capture(self):
+        """Record one batch into a CUDA graph (runs it once eagerly first)."""
+        self.run()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        return g
+
+    def result(self, j):
+        """(count, build_idx, probe_idx) of join j (device tensors, capped at capacity)."""
+        n = int(self.counts[j])
+        m = min(n, int(self.capacities[j]))
+        a, b = int(self.off[j]), int(self.off[j]) + m
+        return n, self.out_bidx[a:b], self.out_pidx[a:b]
+
+
+_TUNED = os.path.join(_HERE, "tuned_batch.json")
+
+
+def load_tuned_batch_knobs() -> "BatchKnobs | None":
+    """Knobs the autotuner stored for this GPU model, if any."""
+    import json
+
+    try:
+        with open(_TUNED) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    try:
+        name = torch.cuda.get_device_name() if torch.cuda.is_available() else None
+    except Exception:
+        name = None
+    if name is not None and d.get("device") not in (None, name):
+        return None
+    k = d.get("knobs", {})
+    return BatchKnobs(int(k.get("block_threads", 256)), int(k.get("chunk_rows", 16384)),
+                      float(k.get("load_factor", 0.5)))

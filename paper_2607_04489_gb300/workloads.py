@@ -18,6 +18,11 @@ whose data is not used):
   permutation of 0..nb-1: span < 2^32, so the keys narrow to uint32) or spread
   over the whole 64-bit range; probe keys drawn from the build keys uniformly or
   Zipf(theta) over a seeded rank order; 8-byte payloads.
+- ``batched_small``: k independent int32 joins; build sizes 2^U(lo, hi)
+  (log-uniform), unique keys a seeded affine bijection of 0..nb-1 on 32 bits,
+  probe = ratio x build rows drawn from the build keys with a per-join
+  power-law skew theta_j ~ U(0, theta_max) (continuous inverse-CDF
+  approximation of Zipf) over a seeded row permutation.
 - ``star_schema``: dimension keys a permutation of 1..n_dim (int32) with int64
   cents payloads in [0, 1e9); fact foreign keys uniform or Zipf over 1..n_dim,
   a seeded fraction replaced by keys absent from the dimension, int64 payloads
@@ -170,3 +175,49 @@ def star_schema(n_dim: int = 150_000_000, n_fact: int = 600_000_000, theta: floa
         del keep
     return JoinInput(dk, dp, fk.to(torch.int32), fp,
                      f"star_schema dim={n_dim} fact={n_fact} theta={theta} sel={selectivity}")
+
+
+@dataclass
+class BatchInput:
+    builds: list
+    probes: list
+    thetas: list
+
+    @property
+    def tuples(self) -> int:
+        return sum(int(b.numel()) for b in self.builds) + sum(int(p.numel()) for p in self.probes)
+
+
+def power_law_ranks(n: int, theta: float, count: int, g: torch.Generator, device) -> torch.Tensor:
+    """0-based ranks with density proportional to (x + 1)^-theta on [0, n),
+    by inverting the continuous power-law CDF (an approximation of Zipf)."""
+    u = torch.rand(count, generator=g, device=device, dtype=torch.float64)
+    if theta == 0.0:
+        r = torch.floor(u * n)
+    else:
+        e = 1.0 - theta
+        r = torch.floor((1.0 + u * ((n + 1.0) ** e - 1.0)) ** (1.0 / e)) - 1.0
+    return r.clamp_(0, n - 1).to(torch.int64)
+
+
+def batched_small(k: int = 4096, log2_lo: float = 10.0, log2_hi: float = 20.0, ratio: int = 4,
+                  theta_max: float = 1.0, seed: int = 0, device="cpu") -> BatchInput:
+    """k independent int32 joins of uneven sizes (see module doc)."""
+    g = _gen(_sub(seed, 0), device)
+    gc = _gen(_sub(seed, 1), "cpu")
+    u = torch.rand(k, generator=gc, dtype=torch.float64)
+    sizes = torch.floor(torch.pow(2.0, log2_lo + (log2_hi - log2_lo) * u)).to(torch.int64).tolist()
+    thetas = (torch.rand(k, generator=gc, dtype=torch.float64) * theta_max).tolist()
+    mults = (torch.randint(0, 1 << 31, (k,), generator=gc, dtype=torch.int64) * 2 + 1).tolist()
+    adds = torch.randint(0, 1 << 32, (k,), generator=gc, dtype=torch.int64).tolist()
+    builds, probes = [], []
+    for j in range(k):
+        nb = max(1, int(sizes[j]))
+        i = torch.arange(nb, device=device, dtype=torch.int64)
+        key = (i * mults[j] + adds[j]) & 0xFFFFFFFF
+        key = torch.where(key >= (1 << 31), key - (1 << 32), key).to(torch.int32)
+        rowperm = torch.randperm(nb, generator=g, device=device)
+        rank = power_law_ranks(nb, thetas[j], ratio * nb, g, device)
+        builds.append(key)
+        probes.append(key[rowperm[rank]])
+    return BatchInput(builds, probes, thetas)

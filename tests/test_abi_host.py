@@ -158,3 +158,18 @@ def test_knob_validation(lib):
     assert so.eiger_join_workspace(100, 100, 7, lib.PHJ2, None, ctypes.byref(ws)) == lib.ERR_INVALID_ARG
     assert so.eiger_join_workspace(-1, 100, lib.I64, lib.PHJ2, None, ctypes.byref(ws)) == lib.ERR_INVALID_ARG
     del cnt
+
+
+def test_batched_workspace_query_needs_no_gpu(lib):
+    descs = (lib.JoinDescT * 3)()
+    for j, (nb, np_) in enumerate([(1000, 4000), (0, 10), (70_000, 5)]):
+        descs[j].nb, descs[j].np = nb, np_
+    ws = ctypes.c_size_t(0)
+    kn = lib.BatchKnobs().to_c()
+    assert lib.load().eiger_join_batched_workspace(descs, 3, lib.I32, ctypes.byref(kn), ctypes.byref(ws)) == 0
+    # tables: 2048 + 0 + 2^18 slots of 8 bytes, plus bookkeeping
+    assert ws.value >= (2048 + (1 << 18)) * 8
+    bad = lib.BatchKnobs(100, 16384, 0.5).to_c()
+    assert lib.load().eiger_join_batched_workspace(descs, 3, lib.I32, ctypes.byref(bad), ctypes.byref(ws)) == lib.ERR_INVALID_ARG
+    st = ctypes.c_int32(0)
+    assert lib.load().eiger_join_batched(lib.I32, None, 3, None, None, None, None, 0, None) == lib.ERR_INVALID_ARG
