@@ -231,6 +231,70 @@ eiger_status eiger_join_batched(eiger_dtype dtype, const eiger_join_desc* d_desc
                                 const eiger_batch_knobs* knobs, void* d_workspace, size_t ws_bytes,
                                 void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned variant selector: a small FP32 network over the runtime statistics
+ * (the paper defers algorithm choice to run time and bases it on statistics,
+ * Sec. 1 and Sec. 4; here the rule is learned from timings). It changes only
+ * which plan runs, never the join result.
+ * ------------------------------------------------------------------------ */
+#define EIGER_MLP_IN 12      /* features, see eiger_features               */
+#define EIGER_MLP_HIDDEN 64
+#define EIGER_MLP_OUT 15     /* plan classes, see eiger_class_plan          */
+
+/* Number of float parameters: W1[64][12] b1[64] W2[64][64] b2[64] W3[15][64] b3[15]. */
+int32_t eiger_mlp_param_count(void);
+
+/* Logits d_logits[n][15] of the network for features d_x[n][12]. Device arrays. */
+eiger_status eiger_mlp_forward(const float* d_params, const float* d_x, int32_t n, float* d_logits,
+                               void* stream);
+
+/* Scratch bytes of eiger_mlp_grad for n samples. */
+eiger_status eiger_mlp_grad_workspace(int32_t n, size_t* bytes);
+
+/*
+ * Mean expected regret L = mean_i sum_c softmax(z_i)_c * d_cost[i][c] and its
+ * gradient with respect to the parameters (d_grad, eiger_mlp_param_count()
+ * floats); d_loss (one float, nullable) receives L. d_cost[i][c] is the
+ * relative slowdown of plan class c on sample i (0 for the fastest class).
+ * Deterministic: per-sample gradients are summed in sample order.
+ */
+eiger_status eiger_mlp_grad(const float* d_params, const float* d_x, const float* d_cost, int32_t n,
+                            float* d_grad, float* d_loss, void* d_workspace, size_t ws_bytes,
+                            void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8); step counts from 1. */
+eiger_status eiger_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int32_t step,
+                            float lr, void* stream);
+
+/*
+ * The 12 selector features of a join (host only): log2 nb, log2 np,
+ * log2(np/nb), key bytes, narrowable, log2(build span + 1),
+ * log2(build NDV estimate + 1), build NDV estimate / nb, log2(probe-sample NDV
+ * estimate + 1), probe-sample NDV estimate / probe-sample rows, fraction of the
+ * probe sample's range inside the build range, log2(non-partitioned table
+ * bytes / L2 bytes). probe_sample: statistics of the first min(np, 2^20) probe
+ * keys (NULL: treated as empty). l2_bytes 0 = the current device's.
+ */
+eiger_status eiger_features(const eiger_stats_t* build, const eiger_stats_t* probe_sample, int64_t nb,
+                            int64_t np, eiger_dtype dtype, size_t l2_bytes, float out[EIGER_MLP_IN]);
+
+/*
+ * Plan of selector class cls (0..14): 0 non-partitioned (load 0.5);
+ * 1..5 one radix pass of 8..12 bits; 6..14 two passes of 10..18 bits in total,
+ * split ceil/floor. narrow is left 0 (the join decides it from the statistics).
+ */
+eiger_status eiger_class_plan(int32_t cls, eiger_plan_t* out);
+
+/*
+ * Makes EIGER_AUTO (with knobs == NULL) choose the plan with the network:
+ * d_params (device, caller-owned, kept until the next call) and per-feature
+ * normalisation x' = (x - mean) / scale (host arrays of 12, copied). The join
+ * then also profiles a probe sample. d_params == NULL restores the rules.
+ * Process-wide setting. Errors: INVALID_ARG.
+ */
+eiger_status eiger_selector_set(const float* d_params, const float* h_feature_mean,
+                                const float* h_feature_scale);
+
 /*
  * eiger_join_static_noalloc -- the static non-partitioned join for callers that
  * cannot allocate device memory. The paper has no counterpart; this entry

@@ -179,6 +179,8 @@ eiger_status check_plan(const eiger_plan_t& p, int64_t nb, int dtype, bool narro
 struct Layout {
     Ctrl* ctrl;
     StatsScratch stats;
+    float* sel_x;  // selector features (one sample)
+    float* sel_z;  // selector logits
     size_t fixed_end;
 };
 
@@ -186,6 +188,8 @@ Layout fixed_layout(Carve& c) {
     Layout l;
     l.ctrl = c.take<Ctrl>(1);
     l.stats = stats_layout(c);
+    l.sel_x = c.take<float>(EIGER_MLP_IN);
+    l.sel_z = c.take<float>(EIGER_MLP_OUT);
     l.fixed_end = c.off;
     return l;
 }
@@ -276,6 +280,45 @@ eiger_status resolve_plan(const JoinCall& c, const eiger_stats_t* bst, eiger_pla
     return EIGER_OK;
 }
 
+constexpr int64_t kProbeSample = 1 << 20;  // probe rows profiled for the selector features
+
+// The learned selector's plan for an AUTO join: profile a probe sample,
+// compute and normalise the features, run the network on the device and take
+// the best-scoring class. *chosen stays false when the class's plan is not
+// valid for these keys (the rules then decide).
+eiger_status learned_plan(const JoinCall& c, const eiger_stats_t& bst, const Layout& lay, const float* params,
+                          const float* mean, const float* scale, eiger_plan_t* pub, bool* chosen) {
+    *chosen = false;
+    static thread_local eiger_stats_t pst;
+    const int64_t nps = c.np < kProbeSample ? c.np : kProbeSample;
+    eiger_status s = run_stats(c.pkeys, nps, c.dtype, lay.stats, c.stream, &pst);
+    if (s != EIGER_OK) return s;
+    float f[EIGER_MLP_IN];
+    compute_features(&bst, &pst, c.nb, c.np, c.dtype, l2_bytes_or_default(), f);
+    for (int i = 0; i < EIGER_MLP_IN; ++i) f[i] = (f[i] - mean[i]) / scale[i];
+    EIGER_CUDA(cudaMemcpyAsync(lay.sel_x, f, sizeof f, cudaMemcpyHostToDevice, c.stream), "selector features");
+    EIGER_CUDA(mlp_forward(params, lay.sel_x, 1, lay.sel_z, c.stream), "selector network");
+    float z[EIGER_MLP_OUT];
+    EIGER_CUDA(cudaMemcpyAsync(z, lay.sel_z, sizeof z, cudaMemcpyDeviceToHost, c.stream), "selector logits");
+    EIGER_CUDA(cudaStreamSynchronize(c.stream), "selector synchronise");
+    int best = 0;
+    for (int k = 1; k < EIGER_MLP_OUT; ++k)
+        if (z[k] > z[best]) best = k;
+    eiger_plan_t p = class_plan(best);
+    const bool nok = narrowable(c.dtype, c.nb, bst.min, bst.max);
+    p.narrow = (c.dtype == EIGER_I32 || nok) ? 1 : 0;
+    const std::string saved = g_last_error;
+    if (check_plan(p, c.nb, c.dtype, nok) != EIGER_OK) {
+        g_last_error = saved;  // an unusable class is not an error: fall back
+        return EIGER_OK;
+    }
+    p.key_min = bst.min;
+    p.key_max = bst.max;
+    *pub = p;
+    *chosen = true;
+    return EIGER_OK;
+}
+
 eiger_status run_join(const JoinCall& c) {
     eiger_status s = validate_common(c);
     if (s != EIGER_OK) return s;
@@ -292,8 +335,18 @@ eiger_status run_join(const JoinCall& c) {
         if (s != EIGER_OK) return s;
     }
     eiger_plan_t pub;
-    s = resolve_plan(c, adaptive ? &bst : nullptr, &pub);
-    if (s != EIGER_OK) return s;
+    bool chosen = false;
+    const float* sel_params;
+    float sel_mean[EIGER_MLP_IN], sel_scale[EIGER_MLP_IN];
+    if (adaptive && c.variant == EIGER_AUTO && !c.knobs && c.nb > 0 && c.np > 0 &&
+        selector_get(&sel_params, sel_mean, sel_scale)) {
+        s = learned_plan(c, bst, lay, sel_params, sel_mean, sel_scale, &pub, &chosen);
+        if (s != EIGER_OK) return s;
+    }
+    if (!chosen) {
+        s = resolve_plan(c, adaptive ? &bst : nullptr, &pub);
+        if (s != EIGER_OK) return s;
+    }
     if (c.plan_used) *c.plan_used = pub;
 
     *c.out_count = 0;
@@ -364,6 +417,12 @@ size_t join_workspace_bytes(int64_t nb, int64_t np, int dtype, int variant, cons
             eiger_plan_t p = plan_rules(variant, nb, np, dtype, nok != 0, l2);
             if (dtype == EIGER_I32) p.narrow = 1;
             consider(p);
+            if (variant == EIGER_AUTO)  // a learned selector may pick any class
+                for (int cls = 0; cls < EIGER_MLP_OUT; ++cls) {
+                    eiger_plan_t q = class_plan(cls);
+                    q.narrow = (dtype == EIGER_I32 || nok) ? 1 : 0;
+                    consider(q);
+                }
         }
     }
     return best;

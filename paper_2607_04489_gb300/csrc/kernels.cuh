@@ -124,6 +124,21 @@ cudaError_t partition_side(const void* keys, int64_t n, int side, const PlanDev&
 cudaError_t phj_run(const JoinArgs& a, const PlanDev& plan, const PhjScratch& s, const JoinOut& out,
                     Ctrl* ctrl, cudaStream_t stream);
 
+// ------------------------------------------------------------------ selector network
+
+int mlp_param_count();
+size_t mlp_grad_ws_bytes(int n);
+cudaError_t mlp_forward(const float* P, const float* X, int n, float* Z, cudaStream_t s);
+cudaError_t mlp_grad(const float* P, const float* X, const float* C, int n, float* grad, float* loss, void* ws,
+                     cudaStream_t s);
+cudaError_t mlp_adam(float* P, const float* grad, float* M, float* V, int step, float lr, cudaStream_t s);
+
+// Learned selector state and helpers (selector.cu).
+bool selector_get(const float** params, float* mean, float* scale);
+void compute_features(const eiger_stats_t* b, const eiger_stats_t* ps, int64_t nb, int64_t np, int dtype,
+                      size_t l2, float* f);
+eiger_plan_t class_plan(int cls);
+
 // ------------------------------------------------------------------ batches
 
 struct BatchLayout {

@@ -120,8 +120,11 @@ _lib = None
 # Every symbol include/eiger.h declares (checked against the header by the tests).
 SYMBOLS = ("eiger_stats_workspace", "eiger_stats", "eiger_plan", "eiger_join_workspace", "eiger_join",
            "eiger_join_sum", "eiger_join_batched_workspace", "eiger_join_batched",
+           "eiger_mlp_param_count", "eiger_mlp_forward", "eiger_mlp_grad_workspace", "eiger_mlp_grad",
+           "eiger_mlp_adam", "eiger_features", "eiger_class_plan", "eiger_selector_set",
            "eiger_join_static_noalloc", "eiger_profile", "eiger_profile_read", "eiger_last_error",
            "eiger_version")
+MLP_IN, MLP_HIDDEN, MLP_OUT = 12, 64, 15
 
 
 def load():
@@ -159,6 +162,23 @@ def load():
                                                  c.POINTER(BatchKnobsT), c.POINTER(sz)]
     lib.eiger_join_batched.restype = c.c_int
     lib.eiger_join_batched.argtypes = [c.c_int, vp, c.c_int32, vp, vp, c.POINTER(BatchKnobsT), vp, sz, vp]
+    fp = c.POINTER(c.c_float)
+    lib.eiger_mlp_param_count.restype = c.c_int32
+    lib.eiger_mlp_param_count.argtypes = []
+    lib.eiger_mlp_forward.restype = c.c_int
+    lib.eiger_mlp_forward.argtypes = [vp, vp, c.c_int32, vp, vp]
+    lib.eiger_mlp_grad_workspace.restype = c.c_int
+    lib.eiger_mlp_grad_workspace.argtypes = [c.c_int32, c.POINTER(sz)]
+    lib.eiger_mlp_grad.restype = c.c_int
+    lib.eiger_mlp_grad.argtypes = [vp, vp, vp, c.c_int32, vp, vp, vp, sz, vp]
+    lib.eiger_mlp_adam.restype = c.c_int
+    lib.eiger_mlp_adam.argtypes = [vp, vp, vp, vp, c.c_int32, c.c_float, vp]
+    lib.eiger_features.restype = c.c_int
+    lib.eiger_features.argtypes = [c.POINTER(StatsT), c.POINTER(StatsT), i64, i64, c.c_int, sz, fp]
+    lib.eiger_class_plan.restype = c.c_int
+    lib.eiger_class_plan.argtypes = [c.c_int32, c.POINTER(PlanT)]
+    lib.eiger_selector_set.restype = c.c_int
+    lib.eiger_selector_set.argtypes = [vp, fp, fp]
     lib.eiger_join_static_noalloc.restype = c.c_int
     lib.eiger_join_static_noalloc.argtypes = [c.c_int, vp, i64, vp, i64, vp, vp, i64, c.POINTER(i64),
                                               vp]
@@ -475,3 +495,69 @@ def load_tuned_batch_knobs() -> "BatchKnobs | None":
     k = d.get("knobs", {})
     return BatchKnobs(int(k.get("block_threads", 256)), int(k.get("chunk_rows", 16384)),
                       float(k.get("load_factor", 0.5)))
+
+
+# ------------------------------------------------------------------ selector network
+
+def mlp_param_count() -> int:
+    return int(load().eiger_mlp_param_count())
+
+
+def mlp_forward(params: torch.Tensor, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """Logits [n, 15] of the selector network (device float32 tensors)."""
+    n = x.shape[0]
+    z = torch.empty((n, MLP_OUT), dtype=torch.float32, device=x.device)
+    _check(load().eiger_mlp_forward(_ptr(params), _ptr(x), n, _ptr(z), _stream(stream)))
+    return z
+
+
+def mlp_grad(params, x, cost, workspace=None, stream=None):
+    """(mean expected regret, gradient) from the library's gradient kernels."""
+    lib = load()
+    n = x.shape[0]
+    if workspace is None:
+        b = ctypes.c_size_t(0)
+        _check(lib.eiger_mlp_grad_workspace(n, ctypes.byref(b)))
+        workspace = torch.empty(max(b.value, 1), dtype=torch.uint8, device=x.device)
+    g = torch.empty_like(params)
+    L = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib.eiger_mlp_grad(_ptr(params), _ptr(x), _ptr(cost), n, _ptr(g), _ptr(L), _ptr(workspace),
+                              workspace.numel(), _stream(stream)))
+    return L, g
+
+
+def mlp_adam(params, grad, m, v, step: int, lr: float, stream=None):
+    _check(load().eiger_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr, _stream(stream)))
+
+
+def features(build: Stats, probe_sample: "Stats | None", nb: int, np_: int, dtype: int,
+             l2_bytes: int = 0) -> np.ndarray:
+    out = (ctypes.c_float * MLP_IN)()
+    b = build.to_c()
+    p = probe_sample.to_c() if probe_sample is not None else None
+    _check(load().eiger_features(ctypes.byref(b), ctypes.byref(p) if p is not None else None, nb, np_, dtype,
+                                 l2_bytes, out))
+    return np.array(out[:], dtype=np.float32)
+
+
+def class_plan(cls: int) -> Plan:
+    p = PlanT()
+    _check(load().eiger_class_plan(cls, ctypes.byref(p)))
+    return Plan.from_c(p)
+
+
+_SELECTOR_KEEP = []
+
+
+def selector_set(params: "torch.Tensor | None", mean=None, scale=None) -> None:
+    """Let EIGER_AUTO use the network (device params kept alive here); None
+    restores the rule-based selector."""
+    lib = load()
+    if params is None:
+        _check(lib.eiger_selector_set(None, None, None))
+        _SELECTOR_KEEP.clear()
+        return
+    m = (ctypes.c_float * MLP_IN)(*[float(v) for v in mean])
+    s = (ctypes.c_float * MLP_IN)(*[float(v) for v in scale])
+    _check(lib.eiger_selector_set(_ptr(params), m, s))
+    _SELECTOR_KEEP[:] = [params]
