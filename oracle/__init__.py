@@ -48,6 +48,9 @@ def _load():
                                  c.POINTER(c.c_int64), c.c_void_p]
     lib.oracle_hll_estimate.restype = c.c_double
     lib.oracle_hll_estimate.argtypes = [c.c_void_p]
+    lib.oracle_groupby.restype = c.c_int64
+    lib.oracle_groupby.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_int, c.c_void_p, c.c_void_p,
+                                   c.c_void_p, c.c_void_p, c.c_void_p, c.c_int64]
     lib.oracle_exact_ndv.restype = c.c_int64
     lib.oracle_exact_ndv.argtypes = [c.c_int, c.c_void_p, c.c_int64]
     _lib = lib
@@ -91,6 +94,16 @@ def join(build_keys, probe_keys, cap=None):
     return out_b[:k].copy(), out_p[:k].copy(), int(n)
 
 
+def join_wide(build_keys, probe_keys, build_cols=(), probe_cols=()):
+    """The wide join in canonical order: (build_idx, probe_idx, build column
+    values, probe column values), where match (i, j) carries row i of every
+    build column and row j of every probe column (Sec. 3.2 materialisation;
+    both strategies compute this same result)."""
+    b, p, _ = join(build_keys, probe_keys)
+    return (b, p, [np.asarray(c)[b.astype(np.int64)] for c in build_cols],
+            [np.asarray(c)[p.astype(np.int64)] for c in probe_cols])
+
+
 def join_count(build_keys, probe_keys) -> int:
     bk, dt = _keys(build_keys)
     pk, _ = _keys(probe_keys)
@@ -131,3 +144,25 @@ def hll_estimate(regs) -> float:
 def exact_ndv(keys) -> int:
     k, dt = _keys(keys)
     return int(_load().oracle_exact_ndv(dt, _ptr(k), k.size))
+
+
+AGG_OPS = {"sum": 0, "count": 1, "min": 2, "max": 3}
+
+
+def groupby(keys, aggs):
+    """Group-by in ascending key order: (keys int64[g], [int64[g] per aggregate]).
+    ``aggs`` is a list of (op, values) with op in sum/count/min/max and values
+    an int32/int64 array (None for count)."""
+    k, dt = _keys(keys)
+    n = k.size
+    ops = np.array([AGG_OPS[o] for o, _ in aggs], np.int32)
+    cols = [np.ascontiguousarray(v) if v is not None else np.zeros(1, np.int64) for _, v in aggs]
+    vb = np.array([c.dtype.itemsize for c in cols], np.int32)
+    ptrs = (ctypes.c_void_p * max(len(cols), 1))(*[c.ctypes.data for c in cols])
+    lib = _load()
+    g = lib.oracle_groupby(dt, _ptr(k), n, len(aggs), ops.ctypes.data, vb.ctypes.data, ptrs, None, None, 0)
+    out_k = np.empty(max(g, 1), np.int64)
+    out_a = np.empty(max(g, 1) * max(len(aggs), 1), np.int64)
+    lib.oracle_groupby(dt, _ptr(k), n, len(aggs), ops.ctypes.data, vb.ctypes.data, ptrs, out_k.ctypes.data,
+                       out_a.ctypes.data, g)
+    return out_k[:g].copy(), [out_a[a * g:(a + 1) * g].copy() for a in range(len(aggs))]

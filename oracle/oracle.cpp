@@ -18,6 +18,8 @@
 //                   counting; statistical accuracy vs 1.04/sqrt(m).
 //   exact ndv       Python set() on small inputs.
 //   min/max         numpy min/max.
+//   group-by        Python dict brute force; sum of counts = rows; sum of
+//                   group sums = column sum; closed forms of i mod g keys.
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -shared -fPIC oracle.cpp
 // (-ffp-contract=off keeps the estimate formula evaluated exactly as written.)
@@ -26,6 +28,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <unordered_map>
 #include <utility>
 #include <vector>
@@ -199,6 +202,52 @@ int64_t oracle_exact_ndv(int dtype, const void* keys, int64_t n) {
     for (int64_t i = 0; i < n; ++i) v[(size_t)i] = key_at(dtype, keys, i);
     std::sort(v.begin(), v.end());
     return (int64_t)(std::unique(v.begin(), v.end()) - v.begin());
+}
+
+// Group-by with aggregates (Sec. 3.3 group-by; Sec. 4.2: the number of groups
+// decides the algorithm). For every distinct key of keys[0, n), in ascending
+// key order: the key and, for each aggregate a, op[a] over the rows of that
+// key of value column vals[a] (vbytes[a] = 4 or 8, sign-extended):
+//   op 0 SUM   (modulo 2^64, returned as int64: exact and order-independent),
+//   op 1 COUNT (rows; vals[a] unused),
+//   op 2 MIN, op 3 MAX (signed).
+// Writes min(groups, cap) groups: out_keys[g], out_aggs[a * cap + g].
+// Returns the number of groups.
+int64_t oracle_groupby(int dtype, const void* keys, int64_t n, int nagg, const int* op, const int* vbytes,
+                       const void* const* vals, int64_t* out_keys, int64_t* out_aggs, int64_t cap) {
+    std::map<int64_t, std::vector<int64_t>> groups;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t k = key_at(dtype, keys, i);
+        auto it = groups.find(k);
+        if (it == groups.end()) {
+            std::vector<int64_t> init(nagg);
+            for (int a = 0; a < nagg; ++a)
+                init[a] = op[a] == 2 ? INT64_MAX : op[a] == 3 ? INT64_MIN : 0;
+            it = groups.emplace(k, init).first;
+        }
+        for (int a = 0; a < nagg; ++a) {
+            int64_t v = 0;
+            if (op[a] != 1) v = vbytes[a] == 4 ? (int64_t)((const int32_t*)vals[a])[i] : ((const int64_t*)vals[a])[i];
+            int64_t& acc = it->second[a];
+            if (op[a] == 0)
+                acc = (int64_t)((uint64_t)acc + (uint64_t)v);
+            else if (op[a] == 1)
+                acc += 1;
+            else if (op[a] == 2)
+                acc = std::min(acc, v);
+            else
+                acc = std::max(acc, v);
+        }
+    }
+    int64_t g = 0;
+    for (const auto& kv : groups) {
+        if (g < cap) {
+            out_keys[g] = kv.first;
+            for (int a = 0; a < nagg; ++a) out_aggs[(int64_t)a * cap + g] = kv.second[a];
+        }
+        ++g;
+    }
+    return g;
 }
 
 }  // extern "C"
