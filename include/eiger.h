@@ -60,10 +60,19 @@ typedef enum {
     EIGER_NPHJ = 1,   /* non-partitioned hash join, global-memory open addressing    */
     EIGER_PHJ1 = 2,   /* radix-partitioned hash join, 1 partitioning pass            */
     EIGER_PHJ2 = 3,   /* radix-partitioned hash join, 2 partitioning passes          */
-    EIGER_STATIC = 4  /* the plain static method: NPHJ with no statistics, no
+    EIGER_STATIC = 4, /* the plain static method: NPHJ with no statistics, no
                          narrowing, load factor 0.5 (the single fixed choice the
                          paper contrasts with adaptivity, Sec. 1 and Sec. 3.2)      */
+    EIGER_SMJ = 5     /* sort-merge join: stable LSD radix sort of both sides on
+                         the (narrowed) key, then a merge (Sec. 3.2, Sec. 5.3).
+                         Chosen only when asked for; the planner never picks it. */
 } eiger_variant;
+
+/* Payload materialisation (Sec. 3.2, after Wu et al.): gather the payload
+ * columns from the untransformed relations by tuple ID (GFUR), or let them go
+ * through the same partitioning / sort as the keys and gather from the
+ * transformed relations by position (GFTR; PHJ and SMJ only). */
+typedef enum { EIGER_GFUR = 0, EIGER_GFTR = 1, EIGER_MAT_AUTO = 2 } eiger_materialize;
 
 #define EIGER_HLL_P 14
 #define EIGER_HLL_M 16384 /* 2^EIGER_HLL_P registers */
@@ -79,15 +88,21 @@ typedef struct {
 
 /* A join plan: the variant and its knobs (Sec. 1 "knob tuning"). */
 typedef struct {
-    int32_t variant;     /* EIGER_NPHJ, EIGER_PHJ1, EIGER_PHJ2 or EIGER_STATIC       */
-    int32_t bits1;       /* PHJ: radix bits of pass 1 (1..12)                        */
-    int32_t bits2;       /* PHJ2: radix bits of pass 2 (1..12); 0 for PHJ1           */
+    int32_t variant;     /* EIGER_NPHJ, EIGER_PHJ1, EIGER_PHJ2, EIGER_STATIC or
+                            EIGER_SMJ                                                */
+    int32_t bits1;       /* PHJ: radix bits of pass 1 (1..12); SMJ: radix bits per
+                            sort pass (1..8, 0 on input = 8)                         */
+    int32_t bits2;       /* PHJ2: radix bits of pass 2 (1..12); 0 for PHJ1; SMJ:
+                            sort passes (set by the library from the key span)       */
     int32_t narrow;      /* 1: keys stored as uint32 offsets from key_min            */
     float load_factor;   /* NPHJ: build rows / table slots, in (0, 0.9]              */
     int32_t selector;    /* who chose: 0 rules, 1 learned model, 2 caller knobs,
                             3 static                                                 */
     int64_t key_min;     /* build-side min/max the plan was made from (filled in by  */
     int64_t key_max;     /* the library; ignored on input)                           */
+    int32_t materialize; /* EIGER_GFUR or EIGER_GFTR: how payloads were gathered
+                            (filled in by the library; ignored on input)             */
+    int32_t reserved;
 } eiger_plan_t;
 
 /*
@@ -183,6 +198,126 @@ eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* 
                             int64_t* out_sum, int64_t* out_count, void* d_workspace,
                             size_t ws_bytes, eiger_plan_t* plan_used, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Wide joins: several payload columns per side (Sec. 3.2 materialisation;
+ * Sec. 5.2 "wide join", four columns per relation).
+ * ------------------------------------------------------------------------ */
+#define EIGER_MAX_COLS 4
+
+/* Payload columns of one side. cols[c]: device, the side's rows; bytes[c]: 4
+ * or 8; out[c]: device, `capacity` entries, receives column c of each match's
+ * row. Only the first n entries are read. */
+typedef struct {
+    int32_t n;
+    int32_t bytes[EIGER_MAX_COLS];
+    const void* cols[EIGER_MAX_COLS];
+    void* out[EIGER_MAX_COLS];
+} eiger_columns;
+
+/*
+ * Scratch bytes eiger_join_wide needs. build/probe: host structs; only n and
+ * bytes are read (NULL = no columns). variant, materialize, knobs as passed to
+ * the join. Errors: INVALID_ARG.
+ */
+eiger_status eiger_join_wide_workspace(int64_t nb, int64_t np, eiger_dtype dtype, const eiger_columns* build,
+                                       const eiger_columns* probe, eiger_variant variant,
+                                       eiger_materialize materialize, const eiger_plan_t* knobs,
+                                       size_t* bytes);
+
+/*
+ * eiger_join_wide -- eiger_join with up to EIGER_MAX_COLS payload columns per
+ * side materialised for every match (Sec. 3.2). Match k is entry k of every
+ * output array: out_bidx / out_pidx (nullable) and each column's out[c].
+ * variant: as eiger_join, plus EIGER_SMJ.
+ * materialize: EIGER_GFUR gathers from the caller's columns by tuple ID (any
+ *          variant). EIGER_GFTR carries the columns through the partitioning
+ *          passes (PHJ1/PHJ2) or the sort passes (SMJ) and gathers them from
+ *          those copies by position; it is rejected for NPHJ/STATIC.
+ *          EIGER_MAT_AUTO takes GFTR for PHJ and SMJ plans and GFUR otherwise.
+ * build, probe: host structs (NULL = no columns); both sides' matched rows
+ *          are gathered for every given column.
+ * plan_used.materialize reports the strategy that ran.
+ * Capacity, counting, synchronisation and errors as eiger_join.
+ */
+eiger_status eiger_join_wide(eiger_dtype dtype, const void* d_bkeys, int64_t nb, const eiger_columns* build,
+                             const void* d_pkeys, int64_t np, const eiger_columns* probe,
+                             eiger_variant variant, eiger_materialize materialize, const eiger_plan_t* knobs,
+                             uint32_t* d_out_bidx, uint32_t* d_out_pidx, int64_t capacity, int64_t* out_count,
+                             void* d_workspace, size_t ws_bytes, eiger_plan_t* plan_used, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Group-by (Sec. 3.3), with the algorithm chosen and the hash table sized
+ * from the HyperLogLog++ estimate of the number of groups (Sec. 4.2).
+ * ------------------------------------------------------------------------ */
+typedef enum {
+    EIGER_GB_AUTO = 0,      /* estimate the groups, then HASH or PARTITION           */
+    EIGER_GB_HASH = 1,      /* one global hash table (CTA-private shared-memory
+                               copies first while it is small)                      */
+    EIGER_GB_PARTITION = 2  /* radix-partition on hashed keys with the value columns
+                               carried along, one shared-memory table per partition */
+} eiger_groupby_variant;
+
+typedef enum { EIGER_AGG_SUM = 0, EIGER_AGG_COUNT = 1, EIGER_AGG_MIN = 2, EIGER_AGG_MAX = 3 } eiger_agg_op;
+
+#define EIGER_MAX_AGGS 4
+
+/* Aggregates of a group-by. Aggregate a applies op[a] to value column vals[a]
+ * (device, n rows of bytes[a] = 4 or 8, signed; unused for COUNT) and writes
+ * one int64 per group to out[a] (device, `capacity` entries). SUM is taken
+ * modulo 2^64; MIN and MAX are signed. */
+typedef struct {
+    int32_t n;
+    int32_t op[EIGER_MAX_AGGS];
+    int32_t bytes[EIGER_MAX_AGGS];
+    const void* vals[EIGER_MAX_AGGS];
+    int64_t* out[EIGER_MAX_AGGS];
+} eiger_aggs;
+
+/* A group-by plan. */
+typedef struct {
+    int32_t variant;      /* EIGER_GB_HASH or EIGER_GB_PARTITION                       */
+    int32_t bits1;        /* PARTITION: radix bits of pass 1 (1..12)                    */
+    int32_t bits2;        /* PARTITION: radix bits of pass 2 (0: one pass; 1..12)      */
+    int32_t narrow;       /* 1: keys carried as uint32 offsets from the minimum         */
+    int64_t table_slots;  /* HASH: slots of the global table (a power of two)           */
+    double estimate;      /* the HyperLogLog++ estimate of the groups (filled in)       */
+    int32_t selector;     /* 0 rules, 2 caller knobs                                    */
+    int32_t attempts;     /* runs needed: 1, or more when a table overflowed because the
+                             estimate was low and the plan was enlarged (filled in)    */
+} eiger_groupby_plan_t;
+
+/*
+ * Scratch bytes eiger_groupby needs for n keys (aggs: host struct; only n,
+ * op and bytes are read). Covers every plan `variant` may take, including the
+ * enlarged plans of a retry. Errors: INVALID_ARG.
+ */
+eiger_status eiger_groupby_workspace(int64_t n, eiger_dtype dtype, const eiger_aggs* aggs, int32_t variant,
+                                     size_t* bytes);
+
+/*
+ * eiger_groupby -- for every distinct key of d_keys[0, n) its aggregates.
+ * Profiles the keys (min/max, HyperLogLog++; Sec. 4.1), narrows them to
+ * uint32 offsets when their span allows (Sec. 4.3), then runs:
+ *   EIGER_GB_AUTO: HASH when a table of 2.5x the estimated groups fits in half
+ *          of the L2 cache, else PARTITION;
+ *   EIGER_GB_HASH: slots = the power of two >= 2.5x the estimate (knobs may
+ *          set table_slots);
+ *   EIGER_GB_PARTITION: 2^B partitions with B = ceil(log2(estimate / 1024)),
+ *          one pass up to 10 bits, else two (knobs may set bits1/bits2).
+ * If a table overflows (an estimate far too low, or caller knobs too small)
+ * the plan is enlarged and the group-by re-run; plan_used->attempts counts the
+ * runs. Groups are written in unspecified order: d_out_keys (dtype, nullable
+ * when capacity is 0) and aggs->out[a]; *out_groups receives the number of
+ * groups. Capacity rules as eiger_join (EIGER_ERR_CAPACITY with the required
+ * count). Synchronises `stream`.
+ * Errors: INVALID_ARG, CAPACITY, WORKSPACE, TABLE_FULL (the largest plan
+ *         still overflowed), CUDA, INTERNAL.
+ */
+eiger_status eiger_groupby(eiger_dtype dtype, const void* d_keys, int64_t n, const eiger_aggs* aggs,
+                           int32_t variant, const eiger_groupby_plan_t* knobs, void* d_out_keys, int64_t capacity,
+                           int64_t* out_groups, void* d_workspace, size_t ws_bytes, eiger_groupby_plan_t* plan_used,
+                           void* stream);
+
 /* One join of a batch (eiger_join_batched). All pointers are device memory. */
 typedef struct {
     const void* build_keys;  /* nb keys of the batch's dtype                 */
@@ -252,14 +387,19 @@ eiger_status eiger_mlp_forward(const float* d_params, const float* d_x, int32_t 
 eiger_status eiger_mlp_grad_workspace(int32_t n, size_t* bytes);
 
 /*
- * Mean expected regret L = mean_i sum_c softmax(z_i)_c * d_cost[i][c] and its
- * gradient with respect to the parameters (d_grad, eiger_mlp_param_count()
- * floats); d_loss (one float, nullable) receives L. d_cost[i][c] is the
- * relative slowdown of plan class c on sample i (0 for the fastest class).
+ * A training loss over the relative slowdowns d_cost[i][c] of plan class c on
+ * sample i (0 for the fastest class), and its gradient with respect to the
+ * parameters (d_grad, eiger_mlp_param_count() floats); d_loss (one float,
+ * nullable) receives the loss.
+ *   tau == 0: the expected regret of the softmax choice,
+ *             mean_i sum_c softmax(z_i)_c d_cost[i][c];
+ *   tau > 0:  the cross-entropy toward the soft target softmax(-d_cost[i] / tau),
+ *             mean_i -sum_c target_ic log softmax(z_i)_c.
  * Deterministic: per-sample gradients are summed in sample order.
+ * Errors: INVALID_ARG (NULL arrays with n > 0, tau < 0 or NaN), WORKSPACE, CUDA.
  */
 eiger_status eiger_mlp_grad(const float* d_params, const float* d_x, const float* d_cost, int32_t n,
-                            float* d_grad, float* d_loss, void* d_workspace, size_t ws_bytes,
+                            float tau, float* d_grad, float* d_loss, void* d_workspace, size_t ws_bytes,
                             void* stream);
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8); step counts from 1. */

@@ -1,10 +1,11 @@
 """CPU oracle for the selector network (test infrastructure only).
 
 Plain numpy in fp64: the 12 -> 64 -> 64 -> 15 multilayer perceptron with ReLU
-hidden layers and a softmax output, its training loss (the expected regret
-of the softmax choice, mean_i sum_c p_ic C_ic, where C_ic is the relative
-slowdown of plan class c on sample i), the gradient by backpropagation, and
-one Adam step. Parameter packing matches the library's: W1[64][12], b1[64],
+hidden layers and a softmax output, its two training losses over the relative
+slowdowns C_ic of plan class c on sample i -- the expected regret of the
+softmax choice, mean_i sum_c p_ic C_ic (tau = 0), and the cross-entropy
+toward the soft target q_i = softmax(-C_i / tau), mean_i -sum_c q_ic log p_ic
+(tau > 0) -- the gradient by backpropagation, and one Adam step. Parameter packing matches the library's: W1[64][12], b1[64],
 W2[64][64], b2[64], W3[15][64], b3[15], each row-major (out x in).
 
 Pinned by tests/test_oracle_mlp_pins.py: central differences of the loss,
@@ -52,20 +53,35 @@ def softmax(z):
     return e / e.sum(axis=1, keepdims=True)
 
 
-def loss(params, X, C):
+def log_softmax(z):
+    s = z - z.max(axis=1, keepdims=True)
+    return s - np.log(np.exp(s).sum(axis=1, keepdims=True))
+
+
+def loss(params, X, C, tau=0.0):
     z, _ = forward(params, X)
-    return float(np.mean(np.sum(softmax(z) * np.asarray(C, dtype=np.float64), axis=1)))
+    C = np.asarray(C, dtype=np.float64)
+    if tau > 0:
+        q = softmax(-C / tau)
+        return float(np.mean(-np.sum(q * log_softmax(z), axis=1)))
+    return float(np.mean(np.sum(softmax(z) * C, axis=1)))
 
 
-def loss_and_grad(params, X, C):
-    """Mean expected regret and its gradient (packed like params)."""
+def loss_and_grad(params, X, C, tau=0.0):
+    """The mean loss (expected regret for tau = 0, soft-target cross-entropy
+    for tau > 0) and its gradient (packed like params)."""
     w = unpack(params)
     C = np.asarray(C, dtype=np.float64)
     n = C.shape[0]
     z, (X, a1, h1, a2, h2) = forward(params, X)
     p = softmax(z)
-    er = np.sum(p * C, axis=1)
-    dz = p * (C - er[:, None]) / n          # d/dz of p . c for a softmax p
+    if tau > 0:
+        q = softmax(-C / tau)
+        per = -np.sum(q * log_softmax(z), axis=1)
+        dz = (p - q) / n                     # d/dz of -q . log softmax(z)
+    else:
+        per = np.sum(p * C, axis=1)
+        dz = p * (C - per[:, None]) / n      # d/dz of p . c for a softmax p
     g = {"W3": dz.T @ h2, "b3": dz.sum(0)}
     dh2 = dz @ w["W3"]
     da2 = dh2 * (a2 > 0)
@@ -75,7 +91,7 @@ def loss_and_grad(params, X, C):
     da1 = dh1 * (a1 > 0)
     g["W1"] = da1.T @ X
     g["b1"] = da1.sum(0)
-    return float(er.mean()), pack(g)
+    return float(per.mean()), pack(g)
 
 
 def adam(params, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):

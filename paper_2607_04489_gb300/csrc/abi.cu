@@ -72,6 +72,7 @@ eiger_status cuda_fail(cudaError_t e, const char* where) {
     } while (0)
 
 constexpr int64_t kMaxRows = 0xFFFFFFFFll;  // rows < 2^32: tuple IDs are uint32
+static_assert(EIGER_MAX_COLS == kMaxCols, "column limit of the ABI and the kernels");
 
 size_t l2_bytes_or_default() {
     DevInfo di;
@@ -133,7 +134,9 @@ PlanDev to_dev(const eiger_plan_t& p, int dtype, const eiger_stats_t* bst) {
     if (bst) {
         d.range.lo = bst->min;
         d.range.hi = bst->max;
-        d.range.offset = d.key32 ? (uint64_t)bst->min : 0ull;
+        // 32-bit keys are offsets from the build minimum; the sort of the
+        // sort-merge join offsets 64-bit keys too, so it orders only the span
+        d.range.offset = (d.key32 || p.variant == EIGER_SMJ) ? (uint64_t)bst->min : 0ull;
         d.check_range = 1;
     } else {
         d.range.lo = INT64_MIN;
@@ -167,8 +170,13 @@ eiger_status check_plan(const eiger_plan_t& p, int64_t nb, int dtype, bool narro
                 return fail(EIGER_ERR_INVALID_ARG, "bits (%d, %d) outside [1, %d] each, sum <= 20",
                             p.bits1, p.bits2, kMaxBits);
             break;
+        case EIGER_SMJ:
+            if (p.bits1 < 0 || p.bits1 > kSortMaxBits)
+                return fail(EIGER_ERR_INVALID_ARG, "SMJ bits1 %d outside [1, %d] (0 = %d)", p.bits1, kSortMaxBits,
+                            kSortMaxBits);
+            break;
         default:
-            return fail(EIGER_ERR_INVALID_ARG, "plan variant %d is not NPHJ/PHJ1/PHJ2/STATIC", p.variant);
+            return fail(EIGER_ERR_INVALID_ARG, "plan variant %d is not NPHJ/PHJ1/PHJ2/STATIC/SMJ", p.variant);
     }
     if (p.narrow != 0 && p.narrow != 1) return fail(EIGER_ERR_INVALID_ARG, "narrow must be 0 or 1");
     if (p.narrow && !narrow_ok)
@@ -195,10 +203,13 @@ Layout fixed_layout(Carve& c) {
 }
 
 size_t variant_bytes(Carve c, int64_t nb, int64_t np, const PlanDev& pd, NphjScratch* ns,
-                     PhjScratch* ps) {
+                     PhjScratch* ps, SmjScratch* ms = nullptr) {
     if (pd.variant == EIGER_NPHJ || pd.variant == EIGER_STATIC) {
         NphjScratch s = nphj_layout(c, nb, pd);
         if (ns) *ns = s;
+    } else if (pd.variant == EIGER_SMJ) {
+        SmjScratch s = smj_layout(c, nb, np, pd);
+        if (ms) *ms = s;
     } else {
         PhjScratch s = phj_layout(c, nb, np, pd);
         if (ps) *ps = s;
@@ -216,6 +227,8 @@ struct JoinCall {
     int64_t np;
     int pay_bytes;
     int variant;
+    int materialize;  // eiger_materialize requested (the narrow calls ask for GFUR)
+    int wide;         // columns come from eiger_columns (bpay/ppay/pay_bytes unused)
     const eiger_plan_t* knobs;
     JoinOut out;
     int64_t* out_count;
@@ -236,25 +249,31 @@ eiger_status validate_common(const JoinCall& c) {
         return fail(EIGER_ERR_INVALID_ARG, "NULL key column with rows");
     if ((c.bkeys && !aligned(c.bkeys, kb)) || (c.pkeys && !aligned(c.pkeys, kb)))
         return fail(EIGER_ERR_INVALID_ARG, "key columns must be aligned to their element size");
-    const bool pay_used = c.bpay || c.ppay || c.out.bpay_out || c.out.ppay_out || c.out.aggregate;
+    const void* bpay_out = !c.wide && c.out.b.n ? c.out.b.dst[0] : nullptr;
+    const void* ppay_out = !c.wide && c.out.p.n ? c.out.p.dst[0] : nullptr;
+    const bool pay_used = c.bpay || c.ppay || bpay_out || ppay_out || c.out.aggregate;
     if (pay_used && c.pay_bytes != 4 && c.pay_bytes != 8)
         return fail(EIGER_ERR_INVALID_ARG, "payload_bytes must be 4 or 8, got %d", c.pay_bytes);
     if (pay_used) {
         const size_t pb = (size_t)c.pay_bytes;
         if ((c.bpay && !aligned(c.bpay, pb)) || (c.ppay && !aligned(c.ppay, pb)) ||
-            (c.out.bpay_out && !aligned(c.out.bpay_out, pb)) || (c.out.ppay_out && !aligned(c.out.ppay_out, pb)))
+            (bpay_out && !aligned(bpay_out, pb)) || (ppay_out && !aligned(ppay_out, pb)))
             return fail(EIGER_ERR_INVALID_ARG, "payload arrays must be aligned to payload_bytes");
     }
-    if ((c.out.bpay_out && !c.bpay) || (c.out.ppay_out && !c.ppay))
+    if ((bpay_out && !c.bpay) || (ppay_out && !c.ppay))
         return fail(EIGER_ERR_INVALID_ARG, "payload output requested without its payload column");
     if ((c.out.bidx && !aligned(c.out.bidx, 4)) || (c.out.pidx && !aligned(c.out.pidx, 4)))
         return fail(EIGER_ERR_INVALID_ARG, "index outputs must be 4-byte aligned");
-    if (c.variant < EIGER_AUTO || c.variant > EIGER_STATIC)
+    if (c.variant < EIGER_AUTO || c.variant > EIGER_SMJ)
         return fail(EIGER_ERR_INVALID_ARG, "bad variant %d", c.variant);
+    if (c.materialize < EIGER_GFUR || c.materialize > EIGER_MAT_AUTO)
+        return fail(EIGER_ERR_INVALID_ARG, "bad materialize %d", c.materialize);
     if (!c.out_count) return fail(EIGER_ERR_INVALID_ARG, "out_count is NULL");
     if (!c.ws && c.ws_bytes) return fail(EIGER_ERR_INVALID_ARG, "NULL workspace with nonzero size");
     return EIGER_OK;
 }
+
+void sort_passes(eiger_plan_t* p);
 
 // Resolves the plan. `bst` holds the build statistics (NULL for STATIC).
 eiger_status resolve_plan(const JoinCall& c, const eiger_stats_t* bst, eiger_plan_t* pub) {
@@ -277,7 +296,48 @@ eiger_status resolve_plan(const JoinCall& c, const eiger_stats_t* bst, eiger_pla
     if (s != EIGER_OK) return s;
     pub->key_min = bst->min;
     pub->key_max = bst->max;
+    if (pub->variant == EIGER_SMJ) sort_passes(pub);
     return EIGER_OK;
+}
+
+// SMJ knobs from the build span: the sort orders the span's significant bits
+// (the keys are offsets from the build minimum) in the fewest passes of at
+// most bits1 bits, with the bits spread evenly over the passes.
+void sort_passes(eiger_plan_t* p) {
+    const int want = p->bits1 ? p->bits1 : kSortMaxBits;
+    PlanDev d{};
+    d.range.lo = p->key_min;
+    d.range.hi = p->key_max;
+    const int sb = sort_key_bits(d);
+    const int passes = sb == 0 ? 1 : (sb + want - 1) / want;
+    p->bits2 = passes;
+    p->bits1 = sb == 0 ? 1 : (sb + passes - 1) / passes;
+}
+
+// Materialisation that runs: GFTR needs a transformation (partitioning or
+// sorting) and at least one column to carry; the aggregate reads payloads by
+// tuple ID.
+eiger_status resolve_materialize(const JoinCall& c, eiger_plan_t* pub) {
+    const bool transformed = pub->variant == EIGER_PHJ1 || pub->variant == EIGER_PHJ2 || pub->variant == EIGER_SMJ;
+    const bool cols = c.out.b.n + c.out.p.n > 0;
+    int m = c.materialize;
+    if (m == EIGER_GFTR && !transformed)
+        return fail(EIGER_ERR_INVALID_ARG, "GFTR needs a partitioned or sort-merge plan (got variant %d)",
+                    pub->variant);
+    if (m == EIGER_MAT_AUTO) m = transformed ? EIGER_GFTR : EIGER_GFUR;
+    if (!cols || c.out.aggregate) m = EIGER_GFUR;
+    pub->materialize = m;
+    return EIGER_OK;
+}
+
+void set_carry(PlanDev& d, const JoinOut& out, int materialize) {
+    d.gftr = materialize == EIGER_GFTR;
+    d.ncols[0] = d.gftr ? out.b.n : 0;
+    d.ncols[1] = d.gftr ? out.p.n : 0;
+    for (int q = 0; q < kMaxCols; ++q) {
+        d.col_bytes[0][q] = q < out.b.n ? out.b.bytes[q] : 0;
+        d.col_bytes[1][q] = q < out.p.n ? out.p.bytes[q] : 0;
+    }
 }
 
 constexpr int64_t kProbeSample = 1 << 20;  // probe rows profiled for the selector features
@@ -347,16 +407,20 @@ eiger_status run_join(const JoinCall& c) {
         s = resolve_plan(c, adaptive ? &bst : nullptr, &pub);
         if (s != EIGER_OK) return s;
     }
+    s = resolve_materialize(c, &pub);
+    if (s != EIGER_OK) return s;
     if (c.plan_used) *c.plan_used = pub;
 
     *c.out_count = 0;
     if (c.out_sum) *c.out_sum = 0;
     if (c.nb == 0 || c.np == 0) return EIGER_OK;
 
-    const PlanDev pd = to_dev(pub, c.dtype, adaptive ? &bst : nullptr);
+    PlanDev pd = to_dev(pub, c.dtype, adaptive ? &bst : nullptr);
+    set_carry(pd, c.out, pub.materialize);
     NphjScratch ns{};
     PhjScratch ps{};
-    const size_t need = variant_bytes(carve, c.nb, c.np, pd, &ns, &ps);
+    SmjScratch ms{};
+    const size_t need = variant_bytes(carve, c.nb, c.np, pd, &ns, &ps, &ms);
     if (need > c.ws_bytes)
         return fail(EIGER_ERR_WORKSPACE, "workspace %zu bytes < %zu needed for this plan", c.ws_bytes, need);
     // Host-side fault injection for tests: EIGER_FAULT=table_full shrinks the
@@ -371,6 +435,8 @@ eiger_status run_join(const JoinCall& c) {
     const JoinArgs a{c.bkeys, c.nb, c.pkeys, c.np};
     if (pd.variant == EIGER_NPHJ || pd.variant == EIGER_STATIC)
         EIGER_CUDA(nphj_run(a, pd, ns, c.out, lay.ctrl, c.stream), "non-partitioned join");
+    else if (pd.variant == EIGER_SMJ)
+        EIGER_CUDA(smj_run(a, pd, ms, c.out, lay.ctrl, c.stream), "sort-merge join");
     else
         EIGER_CUDA(phj_run(a, pd, ps, c.out, lay.ctrl, c.stream), "partitioned join");
 
@@ -388,7 +454,15 @@ eiger_status run_join(const JoinCall& c) {
     return EIGER_OK;
 }
 
-size_t join_workspace_bytes(int64_t nb, int64_t np, int dtype, int variant, const eiger_plan_t* knobs) {
+// Columns a join may carry (GFTR) and the requested materialisation.
+struct ColSpec {
+    int n[2];
+    int bytes[2][kMaxCols];
+    int materialize;
+};
+
+size_t join_workspace_bytes(int64_t nb, int64_t np, int dtype, int variant, const eiger_plan_t* knobs,
+                            const ColSpec& cs) {
     Carve c{nullptr, 0};
     fixed_layout(c);
     size_t best = c.off;
@@ -401,6 +475,16 @@ size_t join_workspace_bytes(int64_t nb, int64_t np, int dtype, int variant, cons
         pd.key32 = dtype == EIGER_I32 || p.narrow;
         pd.load_factor = p.load_factor;
         pd.dtype = dtype;
+        if (p.variant == EIGER_SMJ) {  // the most buffers and counts any key span needs
+            pd.bits1 = p.bits1 ? p.bits1 : kSortMaxBits;
+            pd.bits2 = 2;
+        }
+        const bool transformed = p.variant == EIGER_PHJ1 || p.variant == EIGER_PHJ2 || p.variant == EIGER_SMJ;
+        pd.gftr = transformed && cs.materialize != EIGER_GFUR && cs.n[0] + cs.n[1] > 0;
+        for (int side = 0; side < 2; ++side) {
+            pd.ncols[side] = pd.gftr ? cs.n[side] : 0;
+            for (int q = 0; q < kMaxCols; ++q) pd.col_bytes[side][q] = cs.bytes[side][q];
+        }
         const size_t b = variant_bytes(c, nb, np, pd, nullptr, nullptr);
         if (b > best) best = b;
     };
@@ -415,7 +499,7 @@ size_t join_workspace_bytes(int64_t nb, int64_t np, int dtype, int variant, cons
         const size_t l2 = l2_bytes_or_default();
         for (int nok = 0; nok < 2; ++nok) {
             eiger_plan_t p = plan_rules(variant, nb, np, dtype, nok != 0, l2);
-            if (dtype == EIGER_I32) p.narrow = 1;
+            p.narrow = (dtype == EIGER_I32 || nok) ? 1 : 0;
             consider(p);
             if (variant == EIGER_AUTO)  // a learned selector may pick any class
                 for (int cls = 0; cls < EIGER_MLP_OUT; ++cls) {
@@ -426,6 +510,31 @@ size_t join_workspace_bytes(int64_t nb, int64_t np, int dtype, int variant, cons
         }
     }
     return best;
+}
+
+ColSpec no_columns() {
+    ColSpec cs{};
+    cs.materialize = EIGER_GFUR;
+    return cs;
+}
+
+eiger_status check_columns(const eiger_columns* cols, const char* side, bool need_data, int* n) {
+    *n = 0;
+    if (!cols) return EIGER_OK;
+    if (cols->n < 0 || cols->n > EIGER_MAX_COLS)
+        return fail(EIGER_ERR_INVALID_ARG, "%s: column count %d outside [0, %d]", side, cols->n, EIGER_MAX_COLS);
+    for (int q = 0; q < cols->n; ++q) {
+        const int b = cols->bytes[q];
+        if (b != 4 && b != 8) return fail(EIGER_ERR_INVALID_ARG, "%s column %d: bytes must be 4 or 8", side, q);
+        if (need_data) {
+            if (!cols->cols[q] || !cols->out[q])
+                return fail(EIGER_ERR_INVALID_ARG, "%s column %d: NULL input or output", side, q);
+            if (!aligned(cols->cols[q], b) || !aligned(cols->out[q], b))
+                return fail(EIGER_ERR_INVALID_ARG, "%s column %d: arrays must be aligned to %d bytes", side, q, b);
+        }
+    }
+    *n = cols->n;
+    return EIGER_OK;
 }
 
 }  // namespace
@@ -488,8 +597,8 @@ eiger_status eiger_join_workspace(int64_t nb, int64_t np, eiger_dtype dtype, eig
     if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
     if (nb < 0 || np < 0 || nb > kMaxRows || np > kMaxRows)
         return fail(EIGER_ERR_INVALID_ARG, "row counts must be in [0, 2^32)");
-    if (variant < EIGER_AUTO || variant > EIGER_STATIC) return fail(EIGER_ERR_INVALID_ARG, "bad variant");
-    *bytes = join_workspace_bytes(nb, np, dtype, variant, knobs);
+    if (variant < EIGER_AUTO || variant > EIGER_SMJ) return fail(EIGER_ERR_INVALID_ARG, "bad variant");
+    *bytes = join_workspace_bytes(nb, np, dtype, variant, knobs, no_columns());
     return EIGER_OK;
 }
 
@@ -515,11 +624,14 @@ eiger_status eiger_join(eiger_dtype dtype, const void* d_bkeys, const void* d_bp
     c.knobs = knobs;
     c.out.bidx = d_out_bidx;
     c.out.pidx = d_out_pidx;
-    c.out.bpay_out = d_out_bpay;
-    c.out.ppay_out = d_out_ppay;
-    c.out.bpay = d_bpay;
-    c.out.ppay = d_ppay;
-    c.out.pay_bytes = payload_bytes;
+    c.out.b.src[0] = d_bpay;
+    c.out.b.dst[0] = d_out_bpay;
+    c.out.b.bytes[0] = payload_bytes;
+    c.out.b.n = d_out_bpay ? 1 : 0;
+    c.out.p.src[0] = d_ppay;
+    c.out.p.dst[0] = d_out_ppay;
+    c.out.p.bytes[0] = payload_bytes;
+    c.out.p.n = d_out_ppay ? 1 : 0;
     c.out.aggregate = 0;
     c.out.capacity = (unsigned long long)capacity;
     c.out_count = out_count;
@@ -529,6 +641,296 @@ eiger_status eiger_join(eiger_dtype dtype, const void* d_bkeys, const void* d_bp
     c.plan_used = plan_used;
     c.stream = static_cast<cudaStream_t>(stream);
     return run_join(c);
+}
+
+eiger_status eiger_join_wide_workspace(int64_t nb, int64_t np, eiger_dtype dtype, const eiger_columns* build,
+                                       const eiger_columns* probe, eiger_variant variant,
+                                       eiger_materialize materialize, const eiger_plan_t* knobs,
+                                       size_t* bytes) {
+    if (!bytes) return fail(EIGER_ERR_INVALID_ARG, "bytes is NULL");
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
+    if (nb < 0 || np < 0 || nb > kMaxRows || np > kMaxRows)
+        return fail(EIGER_ERR_INVALID_ARG, "row counts must be in [0, 2^32)");
+    if (variant < EIGER_AUTO || variant > EIGER_SMJ) return fail(EIGER_ERR_INVALID_ARG, "bad variant");
+    if (materialize < EIGER_GFUR || materialize > EIGER_MAT_AUTO)
+        return fail(EIGER_ERR_INVALID_ARG, "bad materialize");
+    ColSpec cs{};
+    cs.materialize = materialize;
+    eiger_status s = check_columns(build, "build", false, &cs.n[0]);
+    if (s == EIGER_OK) s = check_columns(probe, "probe", false, &cs.n[1]);
+    if (s != EIGER_OK) return s;
+    for (int q = 0; q < cs.n[0]; ++q) cs.bytes[0][q] = build->bytes[q];
+    for (int q = 0; q < cs.n[1]; ++q) cs.bytes[1][q] = probe->bytes[q];
+    *bytes = join_workspace_bytes(nb, np, dtype, variant, knobs, cs);
+    return EIGER_OK;
+}
+
+eiger_status eiger_join_wide(eiger_dtype dtype, const void* d_bkeys, int64_t nb, const eiger_columns* build,
+                             const void* d_pkeys, int64_t np, const eiger_columns* probe,
+                             eiger_variant variant, eiger_materialize materialize, const eiger_plan_t* knobs,
+                             uint32_t* d_out_bidx, uint32_t* d_out_pidx, int64_t capacity, int64_t* out_count,
+                             void* d_workspace, size_t ws_bytes, eiger_plan_t* plan_used, void* stream) {
+    if (capacity < 0) return fail(EIGER_ERR_INVALID_ARG, "capacity < 0");
+    int nbc = 0, npc = 0;
+    eiger_status s = check_columns(build, "build", true, &nbc);
+    if (s == EIGER_OK) s = check_columns(probe, "probe", true, &npc);
+    if (s != EIGER_OK) return s;
+    if (capacity > 0 && !d_out_bidx && !d_out_pidx && nbc + npc == 0)
+        return fail(EIGER_ERR_INVALID_ARG, "capacity > 0 but no output array");
+    JoinCall c{};
+    c.dtype = dtype;
+    c.bkeys = d_bkeys;
+    c.nb = nb;
+    c.pkeys = d_pkeys;
+    c.np = np;
+    c.variant = variant;
+    c.materialize = materialize;
+    c.wide = 1;
+    c.knobs = knobs;
+    c.out.bidx = d_out_bidx;
+    c.out.pidx = d_out_pidx;
+    for (int q = 0; q < nbc; ++q) {
+        c.out.b.src[q] = build->cols[q];
+        c.out.b.dst[q] = build->out[q];
+        c.out.b.bytes[q] = build->bytes[q];
+    }
+    c.out.b.n = nbc;
+    for (int q = 0; q < npc; ++q) {
+        c.out.p.src[q] = probe->cols[q];
+        c.out.p.dst[q] = probe->out[q];
+        c.out.p.bytes[q] = probe->bytes[q];
+    }
+    c.out.p.n = npc;
+    c.out.aggregate = 0;
+    c.out.capacity = (unsigned long long)capacity;
+    c.out_count = out_count;
+    c.ws = d_workspace;
+    c.ws_bytes = ws_bytes;
+    c.plan_used = plan_used;
+    c.stream = static_cast<cudaStream_t>(stream);
+    return run_join(c);
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr int kGbTargetGroups = 1024;          // groups per partition the PARTITION plan aims at
+constexpr int kGbMaxBits = 20;                  // most partition bits a retry grows to
+constexpr size_t kGbSmemBudget = 96 * 1024;     // CTA-private hash table limit
+
+unsigned long long pow2_at_least(double x) {
+    unsigned long long s = 64;
+    while ((double)s < x) s <<= 1;
+    return s;
+}
+
+// The most slots a HASH plan (or its retries) may take: a load of 1/2 with
+// every row its own group.
+unsigned long long gb_max_slots(int64_t n) { return pow2_at_least(2.0 * (double)(n > 0 ? n : 1)); }
+
+void gb_split_bits(int B, int32_t* b1, int32_t* b2) {
+    if (B <= 10) {
+        *b1 = B;
+        *b2 = 0;
+    } else {
+        *b1 = (B + 1) / 2;
+        *b2 = B / 2;
+    }
+}
+
+eiger_status check_aggs(const eiger_aggs* aggs, bool need_data) {
+    if (!aggs) return fail(EIGER_ERR_INVALID_ARG, "aggs is NULL");
+    if (aggs->n < 0 || aggs->n > EIGER_MAX_AGGS)
+        return fail(EIGER_ERR_INVALID_ARG, "aggregate count %d outside [0, %d]", aggs->n, EIGER_MAX_AGGS);
+    for (int a = 0; a < aggs->n; ++a) {
+        const int op = aggs->op[a];
+        if (op < EIGER_AGG_SUM || op > EIGER_AGG_MAX)
+            return fail(EIGER_ERR_INVALID_ARG, "aggregate %d: bad op %d", a, op);
+        if (op != EIGER_AGG_COUNT && aggs->bytes[a] != 4 && aggs->bytes[a] != 8)
+            return fail(EIGER_ERR_INVALID_ARG, "aggregate %d: value bytes must be 4 or 8", a);
+        if (need_data) {
+            if (op != EIGER_AGG_COUNT && (!aggs->vals[a] || !aligned(aggs->vals[a], (size_t)aggs->bytes[a])))
+                return fail(EIGER_ERR_INVALID_ARG, "aggregate %d: NULL or misaligned value column", a);
+        }
+    }
+    return EIGER_OK;
+}
+
+// Value-column widths a PARTITION plan carries (COUNT carries none).
+int gb_carried(const eiger_aggs* aggs, int* bytes) {
+    int nc = 0;
+    for (int a = 0; a < aggs->n; ++a)
+        if (aggs->op[a] != EIGER_AGG_COUNT) bytes[nc++] = aggs->bytes[a];
+    return nc;
+}
+
+size_t gb_workspace_bytes(int64_t n, int dtype, const eiger_aggs* aggs, int variant) {
+    Carve c{nullptr, 0};
+    fixed_layout(c);
+    size_t best = c.off;
+    int cb[kMaxCols];
+    const int nc = gb_carried(aggs, cb);
+    for (int key32 = 0; key32 < 2; ++key32) {
+        if (dtype == EIGER_I32 && !key32) continue;
+        GbPlanDev pd{};
+        pd.key32 = key32;
+        pd.naggs = aggs->n;
+        if (variant != EIGER_GB_PARTITION) {
+            pd.variant = EIGER_GB_HASH;
+            pd.slots = gb_max_slots(n);
+            Carve d = c;
+            gb_layout(d, n, pd, cb, nc);
+            if (d.off > best) best = d.off;
+        }
+        if (variant != EIGER_GB_HASH) {
+            pd.variant = EIGER_GB_PARTITION;
+            for (int B = 1; B <= kGbMaxBits; ++B) {
+                gb_split_bits(B, &pd.bits1, &pd.bits2);
+                Carve d = c;
+                gb_layout(d, n, pd, cb, nc);
+                if (d.off > best) best = d.off;
+            }
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+eiger_status eiger_groupby_workspace(int64_t n, eiger_dtype dtype, const eiger_aggs* aggs, int32_t variant,
+                                     size_t* bytes) {
+    if (!bytes) return fail(EIGER_ERR_INVALID_ARG, "bytes is NULL");
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
+    if (n < 0 || n > kMaxRows) return fail(EIGER_ERR_INVALID_ARG, "n must be in [0, 2^32)");
+    if (variant < EIGER_GB_AUTO || variant > EIGER_GB_PARTITION) return fail(EIGER_ERR_INVALID_ARG, "bad variant");
+    eiger_status s = check_aggs(aggs, false);
+    if (s != EIGER_OK) return s;
+    *bytes = gb_workspace_bytes(n, dtype, aggs, variant);
+    return EIGER_OK;
+}
+
+eiger_status eiger_groupby(eiger_dtype dtype, const void* d_keys, int64_t n, const eiger_aggs* aggs,
+                           int32_t variant, const eiger_groupby_plan_t* knobs, void* d_out_keys, int64_t capacity,
+                           int64_t* out_groups, void* d_workspace, size_t ws_bytes, eiger_groupby_plan_t* plan_used,
+                           void* stream) {
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype %d", dtype);
+    if (n < 0 || n > kMaxRows) return fail(EIGER_ERR_INVALID_ARG, "n must be in [0, 2^32)");
+    if (n > 0 && !d_keys) return fail(EIGER_ERR_INVALID_ARG, "NULL keys with n > 0");
+    const size_t kb = dtype == EIGER_I32 ? 4 : 8;
+    if (d_keys && !aligned(d_keys, kb)) return fail(EIGER_ERR_INVALID_ARG, "keys must be aligned to their size");
+    if (variant < EIGER_GB_AUTO || variant > EIGER_GB_PARTITION)
+        return fail(EIGER_ERR_INVALID_ARG, "bad group-by variant %d", variant);
+    if (!out_groups) return fail(EIGER_ERR_INVALID_ARG, "out_groups is NULL");
+    if (capacity < 0) return fail(EIGER_ERR_INVALID_ARG, "capacity < 0");
+    eiger_status s = check_aggs(aggs, n > 0);
+    if (s != EIGER_OK) return s;
+    if (capacity > 0) {
+        if (!d_out_keys || !aligned(d_out_keys, kb))
+            return fail(EIGER_ERR_INVALID_ARG, "capacity > 0 needs an aligned key output");
+        for (int a = 0; a < aggs->n; ++a)
+            if (!aggs->out[a] || !aligned(aggs->out[a], 8))
+                return fail(EIGER_ERR_INVALID_ARG, "aggregate %d: NULL or misaligned output", a);
+    }
+    if (!d_workspace && ws_bytes) return fail(EIGER_ERR_INVALID_ARG, "NULL workspace with nonzero size");
+    if (knobs && variant == EIGER_GB_AUTO) return fail(EIGER_ERR_INVALID_ARG, "knobs need a HASH or PARTITION variant");
+    prof_reset();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Carve carve{static_cast<char*>(d_workspace), 0};
+    Layout lay = fixed_layout(carve);
+    if (lay.fixed_end > ws_bytes)
+        return fail(EIGER_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, lay.fixed_end);
+    static thread_local eiger_stats_t kst;
+    s = run_stats(d_keys, n, dtype, lay.stats, st, &kst);
+    if (s != EIGER_OK) return s;
+
+    eiger_groupby_plan_t pub{};
+    pub.estimate = kst.estimate;
+    pub.narrow = narrowable(dtype, n, kst.min, kst.max) ? 1 : 0;
+    const double est = kst.estimate > 1.0 ? kst.estimate : 1.0;
+    const int keyb = pub.narrow ? 4 : 8;
+    const unsigned long long hash_slots = pow2_at_least(2.5 * est);
+    int v = variant;
+    if (v == EIGER_GB_AUTO) {
+        const double table = (double)hash_slots * (keyb + 8.0 * aggs->n);
+        v = table <= (double)l2_bytes_or_default() / 2 ? EIGER_GB_HASH : EIGER_GB_PARTITION;
+    }
+    pub.variant = v;
+    pub.selector = knobs ? 2 : 0;
+    const unsigned long long max_slots = gb_max_slots(n);
+    if (v == EIGER_GB_HASH) {
+        unsigned long long sl = knobs && knobs->table_slots > 0 ? (unsigned long long)knobs->table_slots : hash_slots;
+        if (sl & (sl - 1)) return fail(EIGER_ERR_INVALID_ARG, "table_slots must be a power of two");
+        pub.table_slots = (int64_t)(sl < max_slots ? sl : max_slots);
+    } else {
+        int B = 1;
+        while (B < kGbMaxBits && est / (double)(1ll << B) > kGbTargetGroups) ++B;
+        if (knobs) {
+            if (knobs->bits1 < 1 || knobs->bits1 > kMaxBits || knobs->bits2 < 0 || knobs->bits2 > kMaxBits ||
+                knobs->bits1 + knobs->bits2 > kGbMaxBits)
+                return fail(EIGER_ERR_INVALID_ARG, "partition bits (%d, %d) outside [1, %d] + [0, %d], sum <= %d",
+                            knobs->bits1, knobs->bits2, kMaxBits, kMaxBits, kGbMaxBits);
+            pub.bits1 = knobs->bits1;
+            pub.bits2 = knobs->bits2;
+        } else {
+            gb_split_bits(B, &pub.bits1, &pub.bits2);
+        }
+    }
+    GbAggs ga{};
+    ga.n = aggs->n;
+    for (int a = 0; a < aggs->n; ++a) {
+        ga.op[a] = aggs->op[a];
+        ga.vals[a] = aggs->vals[a];
+        ga.bytes[a] = aggs->bytes[a];
+        ga.out[a] = reinterpret_cast<long long*>(aggs->out[a]);
+    }
+    int cb[kMaxCols];
+    const int nc = gb_carried(aggs, cb);
+    *out_groups = 0;
+    Ctrl h{};
+    for (int attempt = 1;; ++attempt) {
+        pub.attempts = attempt;
+        GbPlanDev pd{};
+        pd.variant = pub.variant;
+        pd.bits1 = pub.bits1;
+        pd.bits2 = pub.bits2;
+        pd.key32 = pub.narrow;
+        pd.offset = (uint64_t)kst.min;
+        pd.slots = (unsigned long long)pub.table_slots;
+        pd.naggs = aggs->n;
+        pd.smem = pd.variant == EIGER_GB_HASH && gb_smem_table_bytes(pd.slots, aggs->n, pd.key32) <= kGbSmemBudget;
+        Carve c = carve;
+        const GbScratch sc = gb_layout(c, n, pd, cb, nc);
+        if (c.off > ws_bytes)
+            return fail(EIGER_ERR_WORKSPACE, "workspace %zu bytes < %zu needed for this plan", ws_bytes, c.off);
+        if (n == 0) break;
+        EIGER_CUDA(cudaMemsetAsync(lay.ctrl, 0, sizeof(Ctrl), st), "control block reset");
+        EIGER_CUDA(gb_run(GbArgs{d_keys, n, dtype}, pd, sc, ga, d_out_keys, (unsigned long long)capacity, lay.ctrl, st),
+                   "group-by");
+        EIGER_CUDA(cudaMemcpyAsync(&h, lay.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "result readback");
+        EIGER_CUDA(cudaStreamSynchronize(st), "group-by synchronise");
+        if (h.err & kErrInternal) return fail(EIGER_ERR_INTERNAL, "device consistency check failed");
+        if (!(h.err & kErrTableFull)) break;
+        // a table overflowed: enlarge the plan and run again
+        if (pub.variant == EIGER_GB_HASH && (unsigned long long)pub.table_slots < max_slots) {
+            const unsigned long long sl = (unsigned long long)pub.table_slots * 4;
+            pub.table_slots = (int64_t)(sl < max_slots ? sl : max_slots);
+        } else if (pub.variant == EIGER_GB_PARTITION && pub.bits1 + pub.bits2 < kGbMaxBits) {
+            int B = pub.bits1 + pub.bits2 + 2;
+            gb_split_bits(B < kGbMaxBits ? B : kGbMaxBits, &pub.bits1, &pub.bits2);
+        } else {
+            if (plan_used) *plan_used = pub;
+            return fail(EIGER_ERR_TABLE_FULL, "group-by tables overflowed at the largest plan");
+        }
+    }
+    if (plan_used) *plan_used = pub;
+    prof_set_matches(h.cursor);
+    *out_groups = (int64_t)h.cursor;
+    if (h.cursor > (unsigned long long)capacity)
+        return fail(EIGER_ERR_CAPACITY, "%llu groups exceed capacity %lld", h.cursor, (long long)capacity);
+    return EIGER_OK;
 }
 
 namespace {
@@ -621,9 +1023,10 @@ eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* 
     c.pay_bytes = payload_bytes;
     c.variant = variant;
     c.knobs = knobs;
-    c.out.bpay = d_bpay;
-    c.out.ppay = d_ppay;
-    c.out.pay_bytes = payload_bytes;
+    c.out.b.src[0] = d_bpay;
+    c.out.b.bytes[0] = payload_bytes;
+    c.out.p.src[0] = d_ppay;
+    c.out.p.bytes[0] = payload_bytes;
     c.out.aggregate = 1;
     c.out.capacity = 0;
     c.out_count = out_count;

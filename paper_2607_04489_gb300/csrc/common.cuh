@@ -67,7 +67,9 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
 //  - 32-bit: key' = (uint32)(key - offset). offset = build minimum when the
 //    build span fits 32 bits (range-offset narrowing, Sec. 4.3 frame of
 //    reference), or 0 for raw int32 keys (their bit pattern).
-//  - 64-bit: key' = the int64 bit pattern.
+//  - 64-bit: key' = the int64 bit pattern minus offset (mod 2^64): offset 0
+//    for hashing; the build minimum for the sort-merge join, which then
+//    orders only the span's significant bits.
 template <typename KeyT>
 struct KeyCodec;
 
@@ -83,7 +85,7 @@ struct KeyCodec<uint32_t> {
 template <>
 struct KeyCodec<uint64_t> {
     static constexpr int kBits = 64;
-    __device__ __forceinline__ static uint64_t encode(int64_t k, uint64_t) { return (uint64_t)k; }
+    __device__ __forceinline__ static uint64_t encode(int64_t k, uint64_t offset) { return (uint64_t)k - offset; }
     __device__ __forceinline__ static uint64_t hash(uint64_t k) { return mix64(k); }
 };
 
@@ -107,16 +109,28 @@ struct Ctrl {
     unsigned int pad[3];
 };
 
+// Payload columns per side a wide join can materialise.
+constexpr int kMaxCols = 4;
+
+// The payload columns of one side gathered for every match (Sec. 3.2, payload
+// materialisation). With GFUR the sources are the caller's columns and the
+// match carries tuple IDs; with GFTR the sources are the partitioned or
+// sorted copies of the columns and the match carries positions in them, which
+// `rowmap` turns back into tuple IDs for the index outputs.
+struct ColSide {
+    const void* src[kMaxCols];
+    void* dst[kMaxCols];    // outputs, `capacity` rows each
+    int bytes[kMaxCols];    // 4 or 8
+    int n;                  // columns materialised
+    const uint32_t* rowmap; // GFTR: position -> tuple ID; nullptr: matches carry tuple IDs
+};
+
 // Output of one join: materialised arrays or a fused aggregate.
 struct JoinOut {
     uint32_t* bidx;
     uint32_t* pidx;
-    void* bpay_out;
-    void* ppay_out;
-    const void* bpay;  // payload columns gathered by tuple ID (GFUR)
-    const void* ppay;
-    int pay_bytes;
-    int aggregate;  // 1: accumulate sum/count only
+    ColSide b, p;
+    int aggregate;  // 1: accumulate the sum of b.src[0] + p.src[0] and the count only
     unsigned long long capacity;
 };
 

@@ -25,13 +25,26 @@ struct Stage {
     unsigned long long base;
 };
 
+__device__ __forceinline__ void copy_cols(const ColSide& cs, unsigned long long pos, uint32_t i) {
+#pragma unroll 1
+    for (int c = 0; c < cs.n; ++c) {
+        if (cs.bytes[c] == 4)
+            static_cast<uint32_t*>(cs.dst[c])[pos] = __ldg(static_cast<const uint32_t*>(cs.src[c]) + i);
+        else
+            static_cast<unsigned long long*>(cs.dst[c])[pos] =
+                __ldg(static_cast<const unsigned long long*>(cs.src[c]) + i);
+    }
+}
+
+// Writes match `pos` of the output: b and p are tuple IDs, or positions in
+// the transformed relations when the side has a rowmap (GFTR).
 __device__ __forceinline__ void write_match(const JoinOut& out, unsigned long long pos, uint32_t b,
                                             uint32_t p) {
     if (pos >= out.capacity) return;
-    if (out.bidx) out.bidx[pos] = b;
-    if (out.pidx) out.pidx[pos] = p;
-    if (out.bpay_out) write_pay(out.bpay_out, out.pay_bytes, pos, read_pay(out.bpay, out.pay_bytes, b));
-    if (out.ppay_out) write_pay(out.ppay_out, out.pay_bytes, pos, read_pay(out.ppay, out.pay_bytes, p));
+    if (out.bidx) out.bidx[pos] = out.b.rowmap ? __ldg(out.b.rowmap + b) : b;
+    if (out.pidx) out.pidx[pos] = out.p.rowmap ? __ldg(out.p.rowmap + p) : p;
+    copy_cols(out.b, pos, b);
+    copy_cols(out.p, pos, p);
 }
 
 struct AggState {
@@ -45,8 +58,8 @@ __device__ __forceinline__ void emit(Stage<STAGE>& st, AggState& agg, bool has, 
                                      uint32_t p, const JoinOut& out, unsigned long long* cursor) {
     if (AGG) {
         if (has) {
-            agg.sum += (unsigned long long)read_pay(out.bpay, out.pay_bytes, b) +
-                       (unsigned long long)read_pay(out.ppay, out.pay_bytes, p);
+            agg.sum += (unsigned long long)read_pay(out.b.src[0], out.b.bytes[0], b) +
+                       (unsigned long long)read_pay(out.p.src[0], out.p.bytes[0], p);
             agg.count += 1;
         }
         return;

@@ -50,14 +50,17 @@ cudaError_t stats_launch(const void* keys, int64_t n, int dtype, const StatsScra
 
 // Resolved plan handed to the variant launchers.
 struct PlanDev {
-    int variant;      // EIGER_NPHJ / PHJ1 / PHJ2 / STATIC
-    int bits1, bits2;
+    int variant;      // EIGER_NPHJ / PHJ1 / PHJ2 / STATIC / SMJ
+    int bits1, bits2; // PHJ: radix bits per pass; SMJ: digit bits per sort pass, sort passes
     int narrow;       // frame-of-reference narrowing applied (offset = build min)
     int key32;        // keys carried as 32-bit values (int32, or int64 narrowed)
     float load_factor;
     int dtype;        // 0 int32, 1 int64
     KeyRange range;   // build range (probe range test) and encoding offset
     int check_range;  // 1 when `range` holds real statistics
+    int gftr;         // payload columns travel with the keys (GFTR) instead of being gathered by tuple ID
+    int ncols[2];     // GFTR: columns carried per side (build, probe)
+    int col_bytes[2][kMaxCols];
 };
 
 // Inputs of one join, as given to eiger_join.
@@ -97,10 +100,12 @@ struct SegInfo {
     uint32_t start, size, tile_base, ntiles;
 };
 
-// Buffers of one side (build or probe) of the partitioned join.
+// Buffers of one side (build or probe) of the partitioned join or of the
+// sort of the sort-merge join.
 struct PartSide {
     void* key[2];        // ping-pong key buffers (uint32 or uint64 per row)
     uint32_t* idx[2];    // matching tuple-ID buffers
+    void* col[2][kMaxCols];  // GFTR: ping-pong copies of the carried payload columns
     uint32_t* counts;    // per-(tile, digit) counts, scanned in place
     uint32_t* block_sums;
     uint32_t* total;     // [2] kept rows after pass 1 / pass 2
@@ -119,18 +124,97 @@ PhjScratch phj_layout(Carve& c, int64_t nb, int64_t np, const PlanDev& plan);
 
 // Radix-partitions one side into s.key/idx[passes - 1] and fills
 // s.part_start. side: 0 build, 1 probe (only the probe side is range-tested).
+// With plan.gftr the columns `carry->src[0, plan.ncols[side])` travel along
+// into s.col[passes - 1].
 cudaError_t partition_side(const void* keys, int64_t n, int side, const PlanDev& plan,
-                           const PartSide& s, unsigned* err, cudaStream_t stream);
+                           const PartSide& s, const ColSide* carry, unsigned* err, cudaStream_t stream);
+// Carves the buffers of one side: ping-pong keys, tuple IDs and carried
+// columns for `passes` passes, the counts of b1 (+ b2) radix bits, segments,
+// tiles and partition starts (none for a sort, whose passes all take b1 bits).
+void part_side_layout(Carve& c, PartSide& ps, int64_t n, int b1, int b2, int passes, bool sort, size_t kb,
+                      const PlanDev& plan, int side);
+
+// The output of a GFTR join: the payload sources become the transformed
+// copies in buffer `buf` of each side, and the tuple IDs of the index outputs
+// are looked up at the emitted positions.
+inline JoinOut gftr_out(const JoinOut& out, const PartSide& b, const PartSide& p, int buf) {
+    JoinOut o = out;
+    for (int c = 0; c < o.b.n; ++c) o.b.src[c] = b.col[buf][c];
+    for (int c = 0; c < o.p.n; ++c) o.p.src[c] = p.col[buf][c];
+    o.b.rowmap = b.idx[buf];
+    o.p.rowmap = p.idx[buf];
+    return o;
+}
+
+// ------------------------------------------------------------------ SMJ
+
+constexpr int kSortMaxBits = 8;  // digit bits per sort pass
+
+// Significant bits of the encoded build keys (their span), the number of
+// bits a sort must order.
+int sort_key_bits(const PlanDev& plan);
+
+// Stable LSD radix sort of one side on the encoded keys: plan.bits2 passes of
+// plan.bits1 bits from the least significant end; the result (with tuple IDs
+// and carried columns) is in buffer (passes - 1) & 1; s.total[0] = rows kept.
+cudaError_t sort_side(const void* keys, int64_t n, int side, const PlanDev& plan, const PartSide& s,
+                      const ColSide* carry, unsigned* err, cudaStream_t stream);
+
+struct SmjScratch {
+    PartSide side[2];
+    uint32_t* window;  // [chunks][2] build window of every probe chunk
+};
+SmjScratch smj_layout(Carve& c, int64_t nb, int64_t np, const PlanDev& plan);
+cudaError_t smj_run(const JoinArgs& a, const PlanDev& plan, const SmjScratch& s, const JoinOut& out,
+                    Ctrl* ctrl, cudaStream_t stream);
 cudaError_t phj_run(const JoinArgs& a, const PlanDev& plan, const PhjScratch& s, const JoinOut& out,
                     Ctrl* ctrl, cudaStream_t stream);
+
+// ------------------------------------------------------------------ group-by
+
+struct GbArgs {
+    const void* keys;
+    int64_t n;
+    int dtype;
+};
+
+// Resolved group-by plan.
+struct GbPlanDev {
+    int variant;               // EIGER_GB_HASH or EIGER_GB_PARTITION
+    int bits1, bits2;          // partition: radix bits per pass (bits2 = 0: one pass)
+    int key32;                 // keys carried as 32-bit offsets
+    uint64_t offset;           // key minimum (frame of reference)
+    unsigned long long slots;  // hash: global table slots (power of two)
+    int smem;                  // hash: aggregate in a CTA-private shared-memory copy first
+    int naggs;
+};
+
+struct GbAggs {
+    int n;
+    int op[kMaxCols];
+    const void* vals[kMaxCols];
+    int bytes[kMaxCols];
+    long long* out[kMaxCols];
+};
+
+struct GbScratch {
+    void* table;   // hash: keys, aggregates, special flag
+    PartSide part; // partition: the partitioned keys and carried value columns
+};
+
+// Shared-memory bytes of a CTA-private table of `slots` slots.
+size_t gb_smem_table_bytes(unsigned long long slots, int naggs, bool key32);
+GbScratch gb_layout(Carve& c, int64_t n, const GbPlanDev& plan, const int* col_bytes, int ncols);
+cudaError_t gb_run(const GbArgs& g, const GbPlanDev& plan, const GbScratch& s, const GbAggs& aggs, void* out_keys,
+                   unsigned long long capacity, Ctrl* ctrl, cudaStream_t stream);
 
 // ------------------------------------------------------------------ selector network
 
 int mlp_param_count();
 size_t mlp_grad_ws_bytes(int n);
 cudaError_t mlp_forward(const float* P, const float* X, int n, float* Z, cudaStream_t s);
-cudaError_t mlp_grad(const float* P, const float* X, const float* C, int n, float* grad, float* loss, void* ws,
-                     cudaStream_t s);
+cudaError_t mlp_grad(const float* P, const float* X, const float* C, int n, float tau, float* grad, float* loss,
+                     void* ws, cudaStream_t s);
 cudaError_t mlp_adam(float* P, const float* grad, float* M, float* V, int step, float lr, cudaStream_t s);
 
 // Learned selector state and helpers (selector.cu).

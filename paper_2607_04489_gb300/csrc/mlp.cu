@@ -4,9 +4,12 @@
 // are one contiguous float array: W1[64][12], b1[64], W2[64][64], b2[64],
 // W3[15][64], b3[15] (row-major, out x in).
 //
-// Training minimises the expected regret of the softmax choice,
-//   L = mean_i sum_c p_ic * R_ic,  R_ic = t_ic / min_c t_ic - 1 (capped),
-// whose gradient with respect to the logits is p_ic (R_ic - sum_k p_ik R_ik).
+// Two training losses over the relative slowdowns R_ic = t_ic / min_c t_ic - 1
+// (capped) of plan class c on sample i:
+//   tau = 0: the expected regret of the softmax choice,
+//            L = mean_i sum_c p_ic R_ic, dL/dz_ic = p_ic (R_ic - sum_k p_ik R_ik) / n;
+//   tau > 0: the cross-entropy toward the soft target q_i = softmax(-R_i / tau),
+//            L = mean_i -sum_c q_ic log p_ic, dL/dz_ic = (p_ic - q_ic) / n.
 // Kernels: forward (one CTA of 64 threads per sample), per-sample gradients
 // written to a [n][P] buffer and summed in sample order by a second kernel
 // (deterministic), and Adam.
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(kHid)
 // Per-sample loss and gradient (already divided by n) into G[i][P], L[i].
 __global__ void __launch_bounds__(kHid)
     mlp_grad_kernel(const float* __restrict__ P, const float* __restrict__ X, const float* __restrict__ C, int n,
-                    float* __restrict__ G, float* __restrict__ L) {
+                    float tau, float* __restrict__ G, float* __restrict__ L) {
     __shared__ Acts a;
     __shared__ float p[kOut], dz[kOut], da2[kHid], da1[kHid];
     const int t = threadIdx.x;
@@ -89,13 +92,29 @@ __global__ void __launch_bounds__(kHid)
                 p[k] = expf(a.z[k] - m);
                 den += p[k];
             }
-            float er = 0.f;
-            for (int k = 0; k < kOut; ++k) {
-                p[k] /= den;
-                er += p[k] * c[k];
+            for (int k = 0; k < kOut; ++k) p[k] /= den;
+            if (tau > 0.f) {
+                float cmin = c[0];
+                for (int k = 1; k < kOut; ++k) cmin = fminf(cmin, c[k]);
+                float qden = 0.f;
+                for (int k = 0; k < kOut; ++k) {
+                    dz[k] = expf(-(c[k] - cmin) / tau);  // unnormalised target
+                    qden += dz[k];
+                }
+                const float lse = m + logf(den);  // log p_k = z_k - lse
+                float ce = 0.f;
+                for (int k = 0; k < kOut; ++k) {
+                    const float q = dz[k] / qden;
+                    ce -= q * (a.z[k] - lse);
+                    dz[k] = (p[k] - q) * inv_n;
+                }
+                L[i] = ce;
+            } else {
+                float er = 0.f;
+                for (int k = 0; k < kOut; ++k) er += p[k] * c[k];
+                for (int k = 0; k < kOut; ++k) dz[k] = p[k] * (c[k] - er) * inv_n;
+                L[i] = er;
             }
-            for (int k = 0; k < kOut; ++k) dz[k] = p[k] * (c[k] - er) * inv_n;
-            L[i] = er;
         }
         __syncthreads();
         float* g = G + (size_t)i * kP;
@@ -165,13 +184,13 @@ cudaError_t mlp_forward(const float* P, const float* X, int n, float* Z, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t mlp_grad(const float* P, const float* X, const float* C, int n, float* grad, float* loss, void* ws,
-                     cudaStream_t s) {
+cudaError_t mlp_grad(const float* P, const float* X, const float* C, int n, float tau, float* grad, float* loss,
+                     void* ws, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     float* G = static_cast<float*>(ws);
     float* L = reinterpret_cast<float*>(static_cast<char*>(ws) + align_up((size_t)n * kP * sizeof(float), 256));
     const int grid = n < 4096 ? n : 4096;
-    mlp_grad_kernel<<<grid, kHid, 0, s>>>(P, X, C, n, G, L);
+    mlp_grad_kernel<<<grid, kHid, 0, s>>>(P, X, C, n, tau, G, L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     mlp_reduce_kernel<<<(kP + 255) / 256, 256, 0, s>>>(G, L, n, grad, loss);

@@ -39,6 +39,15 @@ constexpr int kScanThreads = 512;
 constexpr int kScanItems = 16;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
+// Payload columns that travel with the keys (GFTR): read at the tile rows of
+// `in`, written to the same output positions as the keys.
+struct ColCarry {
+    const void* in[kMaxCols];
+    void* out[kMaxCols];
+    int bytes[kMaxCols];
+    int n;
+};
+
 template <typename InKey, typename KeyT>
 struct PartPass {
     const InKey* raw;        // pass 1 input: raw key column
@@ -56,6 +65,7 @@ struct PartPass {
     const Tile* tiles;       // nullptr: pass-1 tiling of [0, n)
     const uint32_t* ntiles_dev;
     uint32_t ntiles_fixed;
+    ColCarry cc;
 };
 
 template <typename InKey, typename KeyT>
@@ -90,9 +100,14 @@ __device__ __forceinline__ bool part_load(const PartPass<InKey, KeyT>& a, uint32
     return true;
 }
 
-template <typename KeyT>
+// Partition digit: bits of the mixed key (hash partitioning) or, for the
+// sort, bits of the encoded key itself.
+template <bool SORTM, typename KeyT>
 __device__ __forceinline__ uint32_t digit_of(KeyT k, int dshift, uint32_t dmask) {
-    return (uint32_t)(KeyCodec<KeyT>::hash(k) >> dshift) & dmask;
+    if constexpr (SORTM)
+        return (uint32_t)(k >> dshift) & dmask;
+    else
+        return (uint32_t)(KeyCodec<KeyT>::hash(k) >> dshift) & dmask;
 }
 
 // Exclusive scan of in[0, n) into out[0, n), n <= kPartItems * blockDim.x.
@@ -253,7 +268,7 @@ __host__ __device__ constexpr size_t hist_smem_bytes(int bits) {
            2 * PassIn<InKey, KeyT, FIRST>::kBufBytes;
 }
 
-template <typename InKey, typename KeyT, bool FIRST>
+template <typename InKey, typename KeyT, bool FIRST, bool SORTM>
 __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey, KeyT> a, unsigned* err) {
     using Ring = TileRing<InKey, KeyT, FIRST>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -279,7 +294,8 @@ __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey,
 #pragma unroll 4
         for (uint32_t e = threadIdx.x; e < tl.len; e += kPartThreads) {
             KeyT k;
-            if (tile_key<InKey, KeyT, FIRST>(a, kbuf, e, k)) atomicAdd(&s_cnt[digit_of(k, a.dshift, a.dmask)], 1u);
+            if (tile_key<InKey, KeyT, FIRST>(a, kbuf, e, k))
+                atomicAdd(&s_cnt[digit_of<SORTM>(k, a.dshift, a.dmask)], 1u);
         }
         __syncthreads();
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x)
@@ -297,6 +313,64 @@ __host__ __device__ constexpr size_t scatter_smem_bytes(int bits) {
 
 // Digits a thread owns in the per-tile offset table (prefetched one tile ahead).
 constexpr int kGoffPerThread = (1 << kMaxBits) / kPartThreads;
+
+constexpr int kPartWarps = kPartThreads / kWarp;
+constexpr int kWarpRows = kPartTile / kPartWarps;  // sort scatter: consecutive rows per warp
+static_assert(kWarpRows == kPartItems * kWarp, "sort tiles are warp-blocked");
+
+// Block-collective: moves one carried column of the current tile to the
+// output positions of its rows. Row j of this thread (tile element e_j, digit
+// and rank in dr[j]) is staged at its tile position, then every digit run is
+// written out with consecutive threads on consecutive addresses, like the
+// keys. Hash mode: e_j = j * threads + t, position = start[d] + rank. Sort
+// mode: e_j = warp * kWarpRows + j * 32 + lane, position = start[d] +
+// (rows of digit d in earlier warps) + rank.
+template <bool SORTM, typename V, typename DigT>
+__device__ __forceinline__ void carry_column(const V* __restrict__ src, V* __restrict__ dst,
+                                             const uint32_t (&dr)[kPartItems], const uint16_t* s_wc, uint32_t nd,
+                                             const uint32_t* s_start, const uint32_t* s_goff, const DigT* s_dig,
+                                             uint32_t nk, V* s_col) {
+    const unsigned lane = lane_id();
+    const uint32_t w = threadIdx.x / kWarp;
+#pragma unroll
+    for (int j = 0; j < kPartItems; ++j) {
+        if (dr[j] != kNoDigit) {
+            const uint32_t d = dr[j] & 0xFFFu;
+            uint32_t e, pos;
+            if constexpr (SORTM) {
+                e = w * kWarpRows + j * kWarp + lane;
+                pos = s_start[d] + s_wc[w * nd + d] + (dr[j] >> 12);
+            } else {
+                e = j * kPartThreads + threadIdx.x;
+                pos = s_start[d] + (dr[j] >> 12);
+            }
+            s_col[pos] = __ldcs(src + e);
+        }
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < nk; q += blockDim.x) {
+        const uint32_t d = s_dig[q];
+        dst[s_goff[d] + (q - s_start[d])] = s_col[q];
+    }
+    __syncthreads();
+}
+
+template <bool SORTM, typename DigT>
+__device__ __forceinline__ void carry_columns(const ColCarry& cc, uint32_t tstart, const uint32_t (&dr)[kPartItems],
+                                              const uint16_t* s_wc, uint32_t nd, const uint32_t* s_start,
+                                              const uint32_t* s_goff, const DigT* s_dig, uint32_t nk,
+                                              void* s_stage) {
+#pragma unroll 1
+    for (int c = 0; c < cc.n; ++c) {
+        if (cc.bytes[c] == 4)
+            carry_column<SORTM>(static_cast<const uint32_t*>(cc.in[c]) + tstart, static_cast<uint32_t*>(cc.out[c]),
+                                dr, s_wc, nd, s_start, s_goff, s_dig, nk, static_cast<uint32_t*>(s_stage));
+        else
+            carry_column<SORTM>(static_cast<const unsigned long long*>(cc.in[c]) + tstart,
+                                static_cast<unsigned long long*>(cc.out[c]), dr, s_wc, nd, s_start, s_goff, s_dig,
+                                nk, static_cast<unsigned long long*>(s_stage));
+    }
+}
 
 template <typename InKey, typename KeyT, bool FIRST>
 __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InKey, KeyT> a, unsigned* err) {
@@ -366,7 +440,8 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
         for (int j = 0; j < kPartItems; ++j) {
             const uint32_t e = j * kPartThreads + threadIdx.x;
             dr[j] = kNoDigit;
-            if (e < tl.len && tile_key<InKey, KeyT, FIRST>(a, kbuf, e, kk[j])) dr[j] = digit_of(kk[j], a.dshift, a.dmask);
+            if (e < tl.len && tile_key<InKey, KeyT, FIRST>(a, kbuf, e, kk[j]))
+                dr[j] = digit_of<false>(kk[j], a.dshift, a.dmask);
         }
 #pragma unroll
         for (int j = 0; j < kPartItems; ++j)
@@ -401,6 +476,145 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
             a.out_idx[g] = s_idx[pos];
         }
         __syncthreads();
+        // carried columns reuse the key and row staging (contiguous, >= 8 bytes per row)
+        if (a.cc.n) carry_columns<false>(a.cc, tl.start, dr, nullptr, nd, s_start, s_goff, s_dig, nk, s_key);
+    }
+}
+
+// ------------------------------------------------------------ stable sort scatter
+
+template <typename InKey, typename KeyT, bool FIRST>
+__host__ __device__ constexpr size_t sort_scatter_smem_bytes(int bits) {
+    return align_up(16 + 3 * ((size_t)1 << bits) * sizeof(uint32_t), 16) +
+           2 * PassIn<InKey, KeyT, FIRST>::kBufBytes + align_up((size_t)kPartTile * sizeof(KeyT), 16) +
+           (size_t)kPartTile * sizeof(uint32_t) + (size_t)kPartTile * sizeof(uint8_t) +
+           (size_t)kPartWarps * ((size_t)1 << bits) * sizeof(uint16_t);
+}
+
+// One pass of the stable LSD radix sort (the sort of the sort-merge join,
+// Sec. 3.2). Same three steps as a partitioning pass, but the digit is taken
+// from the key itself and the scatter is stable: every warp owns kWarpRows
+// consecutive rows of the tile and ranks them in order, 32 at a time, with
+// __match_any_sync against its own per-digit counters; the counters of the
+// warps are then scanned in warp order, so rows of equal digit keep their
+// input order within the tile, and the [digit][tile] scan keeps tile order.
+template <typename InKey, typename KeyT, bool FIRST>
+__global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<InKey, KeyT> a, unsigned* err) {
+    using Ring = TileRing<InKey, KeyT, FIRST>;
+    using P = PassIn<InKey, KeyT, FIRST>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_warp[kPartThreads / kWarp];
+    __shared__ uint32_t s_kept;
+    const uint32_t nd = 1u << a.bits;
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + 16);
+    uint32_t* s_start = s_cnt + nd;
+    uint32_t* s_goff = s_start + nd;
+    const size_t ring_off = align_up(16 + 3 * (size_t)nd * 4, 16);
+    const Ring ring = ring_setup<InKey, KeyT, FIRST>(smem, ring_off);
+    KeyT* s_key = reinterpret_cast<KeyT*>(smem + ring_off + 2 * P::kBufBytes);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(s_key) +
+                                                  align_up((size_t)kPartTile * sizeof(KeyT), 16));
+    uint8_t* s_dig = reinterpret_cast<uint8_t*>(s_idx + kPartTile);
+    uint16_t* s_wc = reinterpret_cast<uint16_t*>(s_dig + kPartTile);  // [warp][digit]
+    __syncthreads();
+
+    const unsigned lane = lane_id();
+    const uint32_t w = threadIdx.x / kWarp;
+    const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
+    uint32_t t = blockIdx.x;
+    uint32_t goff[kGoffPerThread];
+    Tile tl_cur;
+    if (t < ntiles) {
+        tl_cur = get_tile(a, t);
+#pragma unroll
+        for (int q = 0; q < kGoffPerThread; ++q) {
+            const uint32_t d = threadIdx.x + q * kPartThreads;
+            goff[q] = d < nd ? a.counts[count_index(tl_cur, t, d, a.bits)] : 0u;
+        }
+    }
+    if (threadIdx.x < kWarp && t < ntiles) ring.issue(a, t, 0);
+    for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const int b = it & 1;
+        const uint32_t tn = t + gridDim.x;
+        if (threadIdx.x < kWarp && tn < ntiles) ring.issue(a, tn, b ^ 1);
+        for (uint32_t d = lane; d < nd; d += kWarp) s_wc[w * nd + d] = 0;
+#pragma unroll
+        for (int q = 0; q < kGoffPerThread; ++q) {
+            const uint32_t d = threadIdx.x + q * kPartThreads;
+            if (d < nd) s_goff[d] = goff[q];
+        }
+        const bool ok = mbar_wait(&ring.bar[b], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            ring_abort(ring, b ^ 1, ((it + 1) >> 1) & 1, tn < ntiles, err);
+            return;
+        }
+        const Tile tl = tl_cur;
+        if (tn < ntiles) {
+            tl_cur = get_tile(a, tn);
+#pragma unroll
+            for (int q = 0; q < kGoffPerThread; ++q) {
+                const uint32_t d = threadIdx.x + q * kPartThreads;
+                goff[q] = d < nd ? a.counts[count_index(tl_cur, tn, d, a.bits)] : 0u;
+            }
+        }
+        const auto* kbuf = ring.keys(b) + lead_of(Ring::key_src(a, tl.start));
+        const uint32_t* rbuf = nullptr;
+        if constexpr (!FIRST) rbuf = ring.rows(b) + lead_of(a.in_idx + tl.start);
+
+        KeyT kk[kPartItems];
+        uint32_t dr[kPartItems];  // (rank within this warp's rows << 12) | digit, or kNoDigit
+#pragma unroll
+        for (int j = 0; j < kPartItems; ++j) {
+            const uint32_t e = w * kWarpRows + j * kWarp + lane;
+            const bool v = e < tl.len && tile_key<InKey, KeyT, FIRST>(a, kbuf, e, kk[j]);
+            const uint32_t d = v ? digit_of<true>(kk[j], a.dshift, a.dmask) : kNoDigit;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = v ? s_wc[w * nd + d] : 0u;
+            __syncwarp();
+            if (v && (int)lane == __ffs(peers) - 1) s_wc[w * nd + d] = (uint16_t)(before + __popc(peers));
+            __syncwarp();
+            dr[j] = v ? ((before + __popc(peers & lanemask_lt())) << 12) | d : kNoDigit;
+        }
+        __syncthreads();
+        // per digit: exclusive prefix over the warps in order, and the tile count
+        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int q = 0; q < kPartWarps; ++q) {
+                const uint32_t c = s_wc[q * nd + d];
+                s_wc[q * nd + d] = (uint16_t)run;
+                run += c;
+            }
+            s_cnt[d] = run;
+        }
+        __syncthreads();
+        const uint32_t kept = block_scan_smem(s_cnt, s_start, nd, s_warp);
+        if (threadIdx.x == 0) s_kept = kept;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPartItems; ++j) {
+            if (dr[j] != kNoDigit) {
+                const uint32_t e = w * kWarpRows + j * kWarp + lane;
+                const uint32_t d = dr[j] & 0xFFFu;
+                const uint32_t pos = s_start[d] + s_wc[w * nd + d] + (dr[j] >> 12);
+                s_key[pos] = kk[j];
+                s_dig[pos] = (uint8_t)d;
+                if constexpr (FIRST)
+                    s_idx[pos] = tl.start + e;
+                else
+                    s_idx[pos] = rbuf[e];
+            }
+        }
+        __syncthreads();
+        const uint32_t nk = s_kept;
+        for (uint32_t pos = threadIdx.x; pos < nk; pos += blockDim.x) {
+            const uint32_t d = s_dig[pos];
+            const uint32_t g = s_goff[d] + (pos - s_start[d]);
+            a.out_key[g] = s_key[pos];
+            a.out_idx[g] = s_idx[pos];
+        }
+        __syncthreads();
+        if (a.cc.n) carry_columns<true>(a.cc, tl.start, dr, s_wc, nd, s_start, s_goff, s_dig, nk, s_key);
     }
 }
 
@@ -606,47 +820,69 @@ cudaError_t scan_counts(uint32_t* counts, ScanLen L, size_t max_len, uint32_t* b
     return cudaGetLastError();
 }
 
-// One partitioning pass over n rows. Algorithmic bytes per launch: the
-// histogram reads each key once; the scatter reads each (key, row) once and
-// writes each kept (key', row) once; the scan reads and writes the counts.
-template <typename InKey, typename KeyT, bool FIRST>
+// Carried-column bytes per row (each is read once and written once per pass).
+inline double carry_bytes(const ColCarry& cc) {
+    double b = 0;
+    for (int c = 0; c < cc.n; ++c) b += cc.bytes[c];
+    return b;
+}
+
+// One partitioning (or sort) pass over n rows. Algorithmic bytes per launch:
+// the histogram reads each key once; the scatter reads each (key, row) once
+// and writes each kept (key', row) once, plus the carried columns; the scan
+// reads and writes the counts.
+template <typename InKey, typename KeyT, bool FIRST, bool SORTM>
 cudaError_t run_pass(PartPass<InKey, KeyT> a, size_t max_tiles, const PartSide& s, uint32_t* total,
-                     unsigned* err, const DevInfo& di, cudaStream_t stream, const char* side_name) {
+                     unsigned* err, const DevInfo& di, cudaStream_t stream, const char* side_name, int pass_no) {
     cudaError_t e;
     const size_t hsmem = hist_smem_bytes<InKey, KeyT, FIRST>(a.bits);
-    const size_t ssmem = scatter_smem_bytes<InKey, KeyT, FIRST>(a.bits);
-    auto hist = part_hist_kernel<InKey, KeyT, FIRST>;
-    auto scat = part_scatter_kernel<InKey, KeyT, FIRST>;
+    const size_t ssmem = SORTM ? sort_scatter_smem_bytes<InKey, KeyT, FIRST>(a.bits)
+                               : scatter_smem_bytes<InKey, KeyT, FIRST>(a.bits);
+    auto hist = part_hist_kernel<InKey, KeyT, FIRST, SORTM>;
+    auto scat = SORTM ? sort_scatter_kernel<InKey, KeyT, FIRST> : part_scatter_kernel<InKey, KeyT, FIRST>;
     if ((e = set_smem(hist, hsmem)) != cudaSuccess) return e;
     if ((e = set_smem(scat, ssmem)) != cudaSuccess) return e;
     const double n = (double)a.n;
     const double in_key = FIRST ? (double)sizeof(InKey) : (double)sizeof(KeyT);
     const double tuple = (double)(sizeof(KeyT) + sizeof(uint32_t));
     const double in_tuple = FIRST ? (double)sizeof(InKey) : tuple;
-    const char* pn = FIRST ? "p1" : "p2";
+    const char* kind = SORTM ? "sort" : "part";
     char name[32];
     {
-        snprintf(name, sizeof name, "part_hist.%s.%s", pn, side_name);
+        snprintf(name, sizeof name, "%s_hist.p%d.%s", kind, pass_no, side_name);
         ProfScope ps(name, n * in_key, stream);
         hist<<<occupancy_grid(hist, kPartThreads, hsmem, di, max_tiles), kPartThreads, hsmem, stream>>>(a, err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     ScanLen L{max_tiles << a.bits, a.tiles ? a.ntiles_dev : nullptr, a.bits};
     {
-        snprintf(name, sizeof name, "part_scan.%s.%s", pn, side_name);
+        snprintf(name, sizeof name, "%s_scan.p%d.%s", kind, pass_no, side_name);
         ProfScope ps(name, 12.0 * (double)(max_tiles << a.bits), stream, 0.0, 3);
         if ((e = scan_counts(a.counts, L, max_tiles << a.bits, s.block_sums, total, stream)) != cudaSuccess)
             return e;
     }
-    snprintf(name, sizeof name, "part_scatter.%s.%s", pn, side_name);
-    ProfScope ps(name, n * (in_tuple + tuple), stream);
+    snprintf(name, sizeof name, "%s_scatter.p%d.%s", kind, pass_no, side_name);
+    ProfScope ps(name, n * (in_tuple + tuple + 2.0 * carry_bytes(a.cc)), stream);
     scat<<<occupancy_grid(scat, kPartThreads, ssmem, di, max_tiles), kPartThreads, ssmem, stream>>>(a, err);
     return cudaGetLastError();
 }
 
+// Carried columns of pass `pass` (0-based) of one side: pass 0 reads the
+// caller's columns, later passes the previous pass's copies.
+ColCarry carry_for(const PlanDev& plan, int side, const ColSide* carry, const PartSide& s, int pass) {
+    ColCarry cc{};
+    cc.n = plan.gftr && carry ? plan.ncols[side] : 0;
+    for (int c = 0; c < cc.n; ++c) {
+        cc.in[c] = pass == 0 ? carry->src[c] : s.col[(pass - 1) & 1][c];
+        cc.out[c] = s.col[pass & 1][c];
+        cc.bytes[c] = plan.col_bytes[side][c];
+    }
+    return cc;
+}
+
 template <typename InKey, typename KeyT>
-cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanDev& plan,
-                            const PartSide& s, unsigned* err, const DevInfo& di, cudaStream_t stream) {
+cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanDev& plan, const PartSide& s,
+                            const ColSide* carry, unsigned* err, const DevInfo& di, cudaStream_t stream) {
     const int passes = plan.variant == 3 ? 2 : 1;
     const int b1 = plan.bits1, b2 = passes == 2 ? plan.bits2 : 0;
     const uint32_t ntiles1 = (n + kPartTile - 1) / kPartTile;
@@ -665,8 +901,9 @@ cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanD
     a.counts = s.counts;
     a.tiles = nullptr;
     a.ntiles_fixed = ntiles1;
+    a.cc = carry_for(plan, side, carry, s, 0);
     const char* sn = side == 0 ? "build" : "probe";
-    if ((e = run_pass<InKey, KeyT, true>(a, ntiles1, s, s.total, err, di, stream, sn)) != cudaSuccess)
+    if ((e = run_pass<InKey, KeyT, true, false>(a, ntiles1, s, s.total, err, di, stream, sn, 1)) != cudaSuccess)
         return e;
 
     if (passes == 2) {
@@ -690,8 +927,9 @@ cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanD
         b.counts = s.counts;
         b.tiles = s.tiles;
         b.ntiles_dev = s.total + 2;
+        b.cc = carry_for(plan, side, carry, s, 1);
         const size_t max_tiles2 = (size_t)ntiles1 + ((size_t)1 << b1);
-        if ((e = run_pass<InKey, KeyT, false>(b, max_tiles2, s, s.total + 1, err, di, stream, sn)) !=
+        if ((e = run_pass<InKey, KeyT, false, false>(b, max_tiles2, s, s.total + 1, err, di, stream, sn, 2)) !=
             cudaSuccess)
             return e;
     }
@@ -702,6 +940,62 @@ cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanD
     part_start_kernel<<<blocks, threads, 0, stream>>>(s.counts, passes, ntiles1, b1, b2, s.segs, s.total,
                                                       s.part_start);
     return cudaGetLastError();
+}
+
+// Stable LSD radix sort of one side (see sort_scatter_kernel): pass 1 reads
+// the raw keys (range test and narrowing as in partitioning) with a fixed
+// tiling; the kept rows then form one segment, tiled once, which every later
+// pass re-reads from the previous pass's buffer.
+template <typename InKey, typename KeyT>
+cudaError_t sort_typed(const InKey* keys, uint32_t n, int side, const PlanDev& plan, const PartSide& s,
+                       const ColSide* carry, unsigned* err, const DevInfo& di, cudaStream_t stream) {
+    const int D = plan.bits1, passes = plan.bits2;
+    const uint32_t ntiles1 = (n + kPartTile - 1) / kPartTile;
+    const char* sn = side == 0 ? "build" : "probe";
+    cudaError_t e;
+    PartPass<InKey, KeyT> a{};
+    a.raw = keys;
+    a.out_key = static_cast<KeyT*>(s.key[0]);
+    a.out_idx = s.idx[0];
+    a.n = n;
+    a.rng = plan.range;
+    a.check_range = side == 1 ? plan.check_range : 0;
+    a.dshift = 0;
+    a.dmask = (1u << D) - 1u;
+    a.bits = D;
+    a.counts = s.counts;
+    a.tiles = nullptr;
+    a.ntiles_fixed = ntiles1;
+    a.cc = carry_for(plan, side, carry, s, 0);
+    if ((e = run_pass<InKey, KeyT, true, true>(a, ntiles1, s, s.total, err, di, stream, sn, 1)) != cudaSuccess)
+        return e;
+    if (passes < 2) return cudaSuccess;
+    {
+        ProfScope ps("seg_tiles", 0.0, stream);
+        seg_tiles_kernel<<<1, 1024, 0, stream>>>(s.counts, ntiles1, 0, s.total, s.segs, s.tiles, s.total + 2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    for (int i = 1; i < passes; ++i) {
+        PartPass<InKey, KeyT> b{};
+        b.in_key = static_cast<const KeyT*>(s.key[(i - 1) & 1]);
+        b.in_idx = s.idx[(i - 1) & 1];
+        b.out_key = static_cast<KeyT*>(s.key[i & 1]);
+        b.out_idx = s.idx[i & 1];
+        b.n = n;
+        b.rng = plan.range;
+        b.check_range = 0;
+        b.dshift = i * D;
+        b.dmask = (1u << D) - 1u;
+        b.bits = D;
+        b.counts = s.counts;
+        b.tiles = s.tiles;
+        b.ntiles_dev = s.total + 2;
+        b.cc = carry_for(plan, side, carry, s, i);
+        if ((e = run_pass<InKey, KeyT, false, true>(b, ntiles1, s, s.total + 1, err, di, stream, sn, i + 1)) !=
+            cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -715,21 +1009,66 @@ size_t part_counts_len(int64_t n, int b1, int b2, int passes) {
 
 size_t part_scan_blocks(size_t counts_len) { return (counts_len + kScanChunk - 1) / kScanChunk + 1; }
 
-cudaError_t partition_side(const void* keys, int64_t n, int side, const PlanDev& plan,
-                           const PartSide& s, unsigned* err, cudaStream_t stream) {
+void part_side_layout(Carve& c, PartSide& ps, int64_t n, int b1, int b2, int passes, bool sort, size_t kb,
+                      const PlanDev& plan, int side) {
+    const int nbuf = passes < 2 ? passes : 2;
+    const int ncols = plan.gftr ? plan.ncols[side] : 0;
+    for (int k = 0; k < 2; ++k) {
+        ps.key[k] = k < nbuf ? c.take<unsigned char>((size_t)n * kb) : nullptr;
+        ps.idx[k] = k < nbuf ? c.take<uint32_t>((size_t)n) : nullptr;
+        for (int q = 0; q < kMaxCols; ++q)
+            ps.col[k][q] = (k < nbuf && q < ncols) ? c.take<unsigned char>((size_t)n * plan.col_bytes[side][q])
+                                                  : nullptr;
+    }
+    const size_t ntiles1 = (size_t)((n + kPartTile - 1) / kPartTile);
+    ps.counts_len = sort ? ntiles1 << b1 : part_counts_len(n, b1, b2, passes);
+    ps.counts = c.take<uint32_t>(ps.counts_len);
+    ps.block_sums = c.take<uint32_t>(part_scan_blocks(ps.counts_len));
+    ps.total = c.take<uint32_t>(4);
+    ps.segs = c.take<SegInfo>(sort ? 1 : (size_t)1 << b1);
+    ps.tiles = c.take<Tile>(passes >= 2 ? ntiles1 + (sort ? 1 : ((size_t)1 << b1)) : 1);
+    ps.part_start = sort ? nullptr : c.take<uint32_t>(((size_t)1 << (b1 + b2)) + 1);
+}
+
+int sort_key_bits(const PlanDev& plan) {
+    const uint64_t span = (uint64_t)plan.range.hi - (uint64_t)plan.range.lo;
+    int b = 0;
+    while (b < 64 && (span >> b) != 0) ++b;
+    return b;
+}
+
+cudaError_t partition_side(const void* keys, int64_t n, int side, const PlanDev& plan, const PartSide& s,
+                           const ColSide* carry, unsigned* err, cudaStream_t stream) {
     DevInfo di;
     cudaError_t e = current_device_info(&di);
     if (e != cudaSuccess) return e;
     const uint32_t nn = (uint32_t)n;
     if (plan.key32) {
         if (plan.dtype == 0)
-            return partition_typed<int32_t, uint32_t>(static_cast<const int32_t*>(keys), nn, side, plan,
-                                                      s, err, di, stream);
-        return partition_typed<int64_t, uint32_t>(static_cast<const int64_t*>(keys), nn, side, plan, s,
+            return partition_typed<int32_t, uint32_t>(static_cast<const int32_t*>(keys), nn, side, plan, s, carry,
+                                                      err, di, stream);
+        return partition_typed<int64_t, uint32_t>(static_cast<const int64_t*>(keys), nn, side, plan, s, carry,
                                                   err, di, stream);
     }
-    return partition_typed<int64_t, uint64_t>(static_cast<const int64_t*>(keys), nn, side, plan, s, err,
+    return partition_typed<int64_t, uint64_t>(static_cast<const int64_t*>(keys), nn, side, plan, s, carry, err,
                                               di, stream);
+}
+
+cudaError_t sort_side(const void* keys, int64_t n, int side, const PlanDev& plan, const PartSide& s,
+                      const ColSide* carry, unsigned* err, cudaStream_t stream) {
+    DevInfo di;
+    cudaError_t e = current_device_info(&di);
+    if (e != cudaSuccess) return e;
+    const uint32_t nn = (uint32_t)n;
+    if (plan.key32) {
+        if (plan.dtype == 0)
+            return sort_typed<int32_t, uint32_t>(static_cast<const int32_t*>(keys), nn, side, plan, s, carry, err,
+                                                 di, stream);
+        return sort_typed<int64_t, uint32_t>(static_cast<const int64_t*>(keys), nn, side, plan, s, carry, err, di,
+                                             stream);
+    }
+    return sort_typed<int64_t, uint64_t>(static_cast<const int64_t*>(keys), nn, side, plan, s, carry, err, di,
+                                         stream);
 }
 
 }  // namespace eiger

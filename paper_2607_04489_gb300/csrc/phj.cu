@@ -198,16 +198,18 @@ struct RoundRegs {
     uint32_t id[Rows<KeyT>::kN];
 };
 
-template <typename KeyT>
+// POS (GFTR): a row is identified by its position in the partitioned arrays
+// (pos0 + i), not by the tuple ID stored beside its key.
+template <bool POS, typename KeyT>
 __device__ __forceinline__ void load_round(RoundRegs<KeyT>& r, const KeyT* __restrict__ key,
                                            const uint32_t* __restrict__ idx, uint32_t base,
-                                           uint32_t n) {
+                                           uint32_t n, uint32_t pos0) {
 #pragma unroll
     for (int j = 0; j < Rows<KeyT>::kN; ++j) {
         const uint32_t i = base + j * kJoinThreads + threadIdx.x;
         if (i < n) {
             r.k[j] = __ldcs(key + i);
-            r.id[j] = __ldcs(idx + i);
+            r.id[j] = POS ? pos0 + i : __ldcs(idx + i);
         }
     }
 }
@@ -302,7 +304,7 @@ __device__ __forceinline__ void flush_positional(Stage<kJoinStage>& st, uint32_t
     if (threadIdx.x == 0) st.count = 0;
 }
 
-template <typename KeyT, bool AGG, bool PAIRS>
+template <typename KeyT, bool AGG, bool PAIRS, bool POS>
 __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
     phj_join_kernel(JoinIn<KeyT> a, JoinOut out, Ctrl* ctrl) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -359,15 +361,16 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
         // Issue the first build and probe loads before clearing the table, so
         // their latency overlaps the clear.
         RoundRegs<KeyT> cur, nxt;
-        load_round(nxt, bkey, bidx, 0, bn);
-        load_round(cur, pkey, pidx, 0, pn);
+        const uint32_t bpos0 = bs0 + bc * kBuildCap, ppos0 = ps0 + pc * kProbeChunk;
+        load_round<POS>(nxt, bkey, bidx, 0, bn, bpos0);
+        load_round<POS>(cur, pkey, pidx, 0, pn, ppos0);
         for (uint32_t i = threadIdx.x; i < tsize; i += kJoinThreads) tab.clear(i);
         __syncthreads();
         // Build. An insert that meets its own key proves a duplicate in this
         // chunk; without one, every probe key has at most one match here.
         int dup = sizeof(KeyT) != 4;  // 64-bit tables cannot see equal keys in flight
         for (uint32_t bb = 0; bb < bn; bb += kRound) {
-            if (bb) load_round(nxt, bkey, bidx, bb, bn);
+            if (bb) load_round<POS>(nxt, bkey, bidx, bb, bn, bpos0);
 #pragma unroll
             for (int j = 0; j < kN; ++j) {
                 if (bb + j * kJoinThreads + threadIdx.x >= bn) continue;
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
 
         for (uint32_t base = 0; base < pn; base += kRound) {
             // the next round's loads are in flight while this round probes
-            if (base + kRound < pn) load_round(nxt, pkey, pidx, base + kRound, pn);
+            if (base + kRound < pn) load_round<POS>(nxt, pkey, pidx, base + kRound, pn, ppos0);
             if (unique) {
                 // Fast path: stop at the first match, no collectives per step.
 #pragma unroll
@@ -435,8 +438,8 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
                     }
                     if (AGG) {
                         if (brow != kHole) {
-                            agg.sum += (unsigned long long)read_pay(out.bpay, out.pay_bytes, brow) +
-                                       (unsigned long long)read_pay(out.ppay, out.pay_bytes, cur.id[j]);
+                            agg.sum += (unsigned long long)read_pay(out.b.src[0], out.b.bytes[0], brow) +
+                                       (unsigned long long)read_pay(out.p.src[0], out.p.bytes[0], cur.id[j]);
                             agg.count += 1;
                         }
                     } else {
@@ -499,10 +502,12 @@ cudaError_t launch_join(const PhjScratch& s, const PlanDev& plan, const JoinOut&
     a.pstart = s.side[1].part_start;
     a.item_prefix = s.item_prefix;
     a.P = 1u << (plan.bits1 + (passes == 2 ? plan.bits2 : 0));
-    const bool pairs = !out.aggregate && out.bidx && out.pidx && !out.bpay_out && !out.ppay_out;
-    auto kern = out.aggregate ? phj_join_kernel<KeyT, true, false>
-                : pairs       ? phj_join_kernel<KeyT, false, true>
-                              : phj_join_kernel<KeyT, false, false>;
+    const bool pairs = !out.aggregate && out.bidx && out.pidx && out.b.n == 0 && out.p.n == 0 && !out.b.rowmap &&
+                       !out.p.rowmap;
+    auto kern = out.aggregate ? phj_join_kernel<KeyT, true, false, false>
+                : pairs       ? phj_join_kernel<KeyT, false, true, false>
+                : plan.gftr   ? phj_join_kernel<KeyT, false, false, true>
+                              : phj_join_kernel<KeyT, false, false, false>;
     // reads every partitioned (key', row) of both sides once, writes the matches
     const double tuple = (double)(sizeof(KeyT) + sizeof(uint32_t));
     ProfScope ps("phj_join", tuple * (double)(nb + np), stream, match_bytes(out));
@@ -525,26 +530,8 @@ PhjScratch phj_layout(Carve& c, int64_t nb, int64_t np, const PlanDev& plan) {
     const int b1 = plan.bits1, b2 = passes == 2 ? plan.bits2 : 0;
     const size_t kb = plan.key32 ? 4 : 8;
     const size_t P = (size_t)1 << (b1 + b2);
-    for (int side = 0; side < 2; ++side) {
-        const int64_t n = side == 0 ? nb : np;
-        PartSide& ps = s.side[side];
-        for (int k = 0; k < 2; ++k) {
-            if (k < passes) {
-                ps.key[k] = c.take<unsigned char>((size_t)n * kb);
-                ps.idx[k] = c.take<uint32_t>((size_t)n);
-            } else {
-                ps.key[k] = nullptr;
-                ps.idx[k] = nullptr;
-            }
-        }
-        ps.counts_len = part_counts_len(n, b1, b2, passes);
-        ps.counts = c.take<uint32_t>(ps.counts_len);
-        ps.block_sums = c.take<uint32_t>(part_scan_blocks(ps.counts_len));
-        ps.total = c.take<uint32_t>(4);
-        ps.segs = c.take<SegInfo>((size_t)1 << b1);
-        ps.tiles = c.take<Tile>(passes == 2 ? (size_t)((n + kPartTile - 1) / kPartTile) + ((size_t)1 << b1) : 1);
-        ps.part_start = c.take<uint32_t>(P + 1);
-    }
+    part_side_layout(c, s.side[0], nb, b1, b2, passes, false, kb, plan, 0);
+    part_side_layout(c, s.side[1], np, b1, b2, passes, false, kb, plan, 1);
     s.item_prefix = c.take<unsigned long long>(P + 1);
     return s;
 }
@@ -555,11 +542,13 @@ cudaError_t phj_run(const JoinArgs& a, const PlanDev& plan, const PhjScratch& s,
     DevInfo di;
     cudaError_t e = current_device_info(&di);
     if (e != cudaSuccess) return e;
-    if ((e = partition_side(a.bkeys, a.nb, 0, plan, s.side[0], &ctrl->err, stream)) != cudaSuccess)
+    if ((e = partition_side(a.bkeys, a.nb, 0, plan, s.side[0], &out.b, &ctrl->err, stream)) != cudaSuccess)
         return e;
-    if ((e = partition_side(a.pkeys, a.np, 1, plan, s.side[1], &ctrl->err, stream)) != cudaSuccess)
+    if ((e = partition_side(a.pkeys, a.np, 1, plan, s.side[1], &out.p, &ctrl->err, stream)) != cudaSuccess)
         return e;
     const int passes = plan.variant == 3 ? 2 : 1;
+    // GFTR: gather from the partitioned copies at the positions the join emits
+    const JoinOut o = plan.gftr ? gftr_out(out, s.side[0], s.side[1], passes - 1) : out;
     const uint32_t P = 1u << (plan.bits1 + (passes == 2 ? plan.bits2 : 0));
     {
         ProfScope ps("phj_items", 32.0 * P, stream, 0.0, 2);
@@ -568,8 +557,8 @@ cudaError_t phj_run(const JoinArgs& a, const PlanDev& plan, const PhjScratch& s,
         items_scan_kernel<<<1, 1024, 0, stream>>>(s.item_prefix, P, ctrl);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return plan.key32 ? launch_join<uint32_t>(s, plan, out, ctrl, di, stream, a.nb, a.np)
-                      : launch_join<uint64_t>(s, plan, out, ctrl, di, stream, a.nb, a.np);
+    return plan.key32 ? launch_join<uint32_t>(s, plan, o, ctrl, di, stream, a.nb, a.np)
+                      : launch_join<uint64_t>(s, plan, o, ctrl, di, stream, a.nb, a.np);
 }
 
 }  // namespace eiger

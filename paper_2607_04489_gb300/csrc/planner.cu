@@ -71,6 +71,9 @@ eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool nar
             p.bits1 = 1;
             p.bits2 = 1;
         }
+    } else if (v == EIGER_SMJ) {
+        p.bits1 = 8;  // digit bits per sort pass; the passes follow from the key span
+        p.bits2 = 0;
     }
     return p;
 }

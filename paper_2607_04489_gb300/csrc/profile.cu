@@ -66,12 +66,12 @@ void prof_reset() {
 void prof_set_matches(unsigned long long m) { g_prof.matches = m; }
 
 double match_bytes(const JoinOut& out) {
-    if (out.aggregate) return 2.0 * out.pay_bytes;  // both payloads read per match
+    if (out.aggregate) return 2.0 * out.b.bytes[0];  // both payloads read per match
     double b = 0;
-    if (out.bidx) b += 4;
-    if (out.pidx) b += 4;
-    if (out.bpay_out) b += 2.0 * out.pay_bytes;  // gathered and written
-    if (out.ppay_out) b += 2.0 * out.pay_bytes;
+    if (out.bidx) b += out.b.rowmap ? 8 : 4;  // (rowmap read +) index written
+    if (out.pidx) b += out.p.rowmap ? 8 : 4;
+    for (int c = 0; c < out.b.n; ++c) b += 2.0 * out.b.bytes[c];  // gathered and written
+    for (int c = 0; c < out.p.n; ++c) b += 2.0 * out.p.bytes[c];
     return b;
 }
 int prof_count() { return g_prof.used; }

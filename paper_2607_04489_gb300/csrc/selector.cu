@@ -98,12 +98,13 @@ eiger_status eiger_mlp_grad_workspace(int32_t n, size_t* bytes) {
     return EIGER_OK;
 }
 
-eiger_status eiger_mlp_grad(const float* d_params, const float* d_x, const float* d_cost, int32_t n, float* d_grad,
-                            float* d_loss, void* d_ws, size_t ws_bytes, void* stream) {
+eiger_status eiger_mlp_grad(const float* d_params, const float* d_x, const float* d_cost, int32_t n, float tau,
+                            float* d_grad, float* d_loss, void* d_ws, size_t ws_bytes, void* stream) {
     if (n < 0 || (n > 0 && (!d_params || !d_x || !d_cost || !d_grad || !d_ws)))
         return report_error(EIGER_ERR_INVALID_ARG, "bad network arguments");
+    if (!(tau >= 0.f)) return report_error(EIGER_ERR_INVALID_ARG, "tau must be >= 0");
     if (ws_bytes < mlp_grad_ws_bytes(n)) return report_error(EIGER_ERR_WORKSPACE, "workspace too small");
-    cudaError_t e = mlp_grad(d_params, d_x, d_cost, n, d_grad, d_loss, d_ws, static_cast<cudaStream_t>(stream));
+    cudaError_t e = mlp_grad(d_params, d_x, d_cost, n, tau, d_grad, d_loss, d_ws, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? EIGER_OK : report_error(EIGER_ERR_CUDA, cudaGetErrorString(e));
 }
 

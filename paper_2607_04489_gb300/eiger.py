@@ -22,8 +22,12 @@ LIB_PATH = os.path.join(_HERE, "libeiger.so")
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_WORKSPACE, ERR_TABLE_FULL, ERR_CUDA, ERR_INTERNAL = range(7)
 I32, I64 = 0, 1
-AUTO, NPHJ, PHJ1, PHJ2, STATIC = range(5)
-VARIANTS = {"auto": AUTO, "nphj": NPHJ, "phj1": PHJ1, "phj2": PHJ2, "static": STATIC}
+AUTO, NPHJ, PHJ1, PHJ2, STATIC, SMJ = range(6)
+VARIANTS = {"auto": AUTO, "nphj": NPHJ, "phj1": PHJ1, "phj2": PHJ2, "static": STATIC, "smj": SMJ}
+GFUR, GFTR, MAT_AUTO = range(3)
+MATERIALIZE = {"gfur": GFUR, "gftr": GFTR, "auto": MAT_AUTO}
+MATERIALIZE_NAMES = {GFUR: "gfur", GFTR: "gftr"}
+MAX_COLS = 4
 VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
 HLL_M = 16384
 
@@ -69,7 +73,55 @@ class PlanT(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("bits1", ctypes.c_int32), ("bits2", ctypes.c_int32),
                 ("narrow", ctypes.c_int32), ("load_factor", ctypes.c_float),
                 ("selector", ctypes.c_int32), ("key_min", ctypes.c_int64),
-                ("key_max", ctypes.c_int64)]
+                ("key_max", ctypes.c_int64), ("materialize", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+MAX_AGGS = 4
+GB_AUTO, GB_HASH, GB_PARTITION = range(3)
+GB_VARIANTS = {"auto": GB_AUTO, "hash": GB_HASH, "partition": GB_PARTITION}
+GB_VARIANT_NAMES = {v: k for k, v in GB_VARIANTS.items()}
+AGG_SUM, AGG_COUNT, AGG_MIN, AGG_MAX = range(4)
+AGG_OPS = {"sum": AGG_SUM, "count": AGG_COUNT, "min": AGG_MIN, "max": AGG_MAX}
+
+
+class AggsT(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("op", ctypes.c_int32 * MAX_AGGS), ("bytes", ctypes.c_int32 * MAX_AGGS),
+                ("vals", ctypes.c_void_p * MAX_AGGS), ("out", ctypes.c_void_p * MAX_AGGS)]
+
+
+class GbPlanT(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("bits1", ctypes.c_int32), ("bits2", ctypes.c_int32),
+                ("narrow", ctypes.c_int32), ("table_slots", ctypes.c_int64), ("estimate", ctypes.c_double),
+                ("selector", ctypes.c_int32), ("attempts", ctypes.c_int32)]
+
+
+@dataclass
+class GbPlan:
+    variant: str
+    bits1: int = 0
+    bits2: int = 0
+    narrow: int = 0
+    table_slots: int = 0
+    estimate: float = 0.0
+    selector: int = 0
+    attempts: int = 0
+
+    @classmethod
+    def from_c(cls, p: "GbPlanT") -> "GbPlan":
+        return cls(GB_VARIANT_NAMES.get(p.variant, str(p.variant)), p.bits1, p.bits2, p.narrow, p.table_slots,
+                   p.estimate, p.selector, p.attempts)
+
+    def to_c(self) -> "GbPlanT":
+        p = GbPlanT()
+        p.variant = GB_VARIANTS[self.variant]
+        p.bits1, p.bits2, p.narrow, p.table_slots = self.bits1, self.bits2, self.narrow, self.table_slots
+        return p
+
+
+class ColumnsT(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("bytes", ctypes.c_int32 * MAX_COLS),
+                ("cols", ctypes.c_void_p * MAX_COLS), ("out", ctypes.c_void_p * MAX_COLS)]
 
 
 @dataclass
@@ -101,11 +153,13 @@ class Plan:
     selector: int = 0
     key_min: int = 0
     key_max: int = 0
+    materialize: str = "gfur"
 
     @classmethod
     def from_c(cls, p: PlanT) -> "Plan":
         return cls(VARIANT_NAMES.get(p.variant, str(p.variant)), p.bits1, p.bits2, p.narrow,
-                   p.load_factor, p.selector, p.key_min, p.key_max)
+                   p.load_factor, p.selector, p.key_min, p.key_max,
+                   MATERIALIZE_NAMES.get(p.materialize, str(p.materialize)))
 
     def to_c(self) -> PlanT:
         p = PlanT()
@@ -123,7 +177,8 @@ SYMBOLS = ("eiger_stats_workspace", "eiger_stats", "eiger_plan", "eiger_join_wor
            "eiger_mlp_param_count", "eiger_mlp_forward", "eiger_mlp_grad_workspace", "eiger_mlp_grad",
            "eiger_mlp_adam", "eiger_features", "eiger_class_plan", "eiger_selector_set",
            "eiger_join_static_noalloc", "eiger_profile", "eiger_profile_read", "eiger_last_error",
-           "eiger_version")
+           "eiger_version", "eiger_join_wide_workspace", "eiger_join_wide", "eiger_groupby_workspace",
+           "eiger_groupby")
 MLP_IN, MLP_HIDDEN, MLP_OUT = 12, 64, 15
 
 
@@ -157,6 +212,18 @@ def load():
     lib.eiger_join_sum.argtypes = [c.c_int, vp, vp, i64, vp, vp, i64, i32, c.c_int,
                                    c.POINTER(PlanT), c.POINTER(i64), c.POINTER(i64), vp, sz,
                                    c.POINTER(PlanT), vp]
+    lib.eiger_join_wide_workspace.restype = c.c_int
+    lib.eiger_join_wide_workspace.argtypes = [i64, i64, c.c_int, c.POINTER(ColumnsT), c.POINTER(ColumnsT),
+                                              c.c_int, c.c_int, c.POINTER(PlanT), c.POINTER(sz)]
+    lib.eiger_join_wide.restype = c.c_int
+    lib.eiger_join_wide.argtypes = [c.c_int, vp, i64, c.POINTER(ColumnsT), vp, i64, c.POINTER(ColumnsT),
+                                    c.c_int, c.c_int, c.POINTER(PlanT), vp, vp, i64, c.POINTER(i64), vp, sz,
+                                    c.POINTER(PlanT), vp]
+    lib.eiger_groupby_workspace.restype = c.c_int
+    lib.eiger_groupby_workspace.argtypes = [i64, c.c_int, c.POINTER(AggsT), c.c_int32, c.POINTER(sz)]
+    lib.eiger_groupby.restype = c.c_int
+    lib.eiger_groupby.argtypes = [c.c_int, vp, i64, c.POINTER(AggsT), c.c_int32, c.POINTER(GbPlanT), vp, i64,
+                                  c.POINTER(i64), vp, sz, c.POINTER(GbPlanT), vp]
     lib.eiger_join_batched_workspace.restype = c.c_int
     lib.eiger_join_batched_workspace.argtypes = [c.POINTER(JoinDescT), c.c_int32, c.c_int,
                                                  c.POINTER(BatchKnobsT), c.POINTER(sz)]
@@ -170,7 +237,7 @@ def load():
     lib.eiger_mlp_grad_workspace.restype = c.c_int
     lib.eiger_mlp_grad_workspace.argtypes = [c.c_int32, c.POINTER(sz)]
     lib.eiger_mlp_grad.restype = c.c_int
-    lib.eiger_mlp_grad.argtypes = [vp, vp, vp, c.c_int32, vp, vp, vp, sz, vp]
+    lib.eiger_mlp_grad.argtypes = [vp, vp, vp, c.c_int32, c.c_float, vp, vp, vp, sz, vp]
     lib.eiger_mlp_adam.restype = c.c_int
     lib.eiger_mlp_adam.argtypes = [vp, vp, vp, vp, c.c_int32, c.c_float, vp]
     lib.eiger_features.restype = c.c_int
@@ -378,6 +445,178 @@ def join_sum(build_keys, build_pay, probe_keys, probe_pay, *, variant="auto",
     return s.value, cnt.value, Plan.from_c(used)
 
 
+def _columns(cols, outs=None) -> ColumnsT | None:
+    """eiger_columns of one side from a list of 4- or 8-byte device tensors
+    (and the matching output tensors)."""
+    if not cols:
+        return None
+    if len(cols) > MAX_COLS:
+        raise ValueError(f"at most {MAX_COLS} payload columns per side")
+    c = ColumnsT()
+    c.n = len(cols)
+    for q, t in enumerate(cols):
+        c.bytes[q] = t.element_size()
+        c.cols[q] = t.data_ptr() if t.numel() else None
+        if outs is not None:
+            c.out[q] = outs[q].data_ptr() if outs[q].numel() else None
+    return c
+
+
+def _mat(m) -> int:
+    return MATERIALIZE[m] if isinstance(m, str) else int(m)
+
+
+def join_wide_workspace(nb: int, np_: int, dtype: int, build_cols=(), probe_cols=(), variant="auto",
+                        materialize="auto", knobs: Plan | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    b, p = _columns(list(build_cols)), _columns(list(probe_cols))
+    k = knobs.to_c() if knobs is not None else None
+    _check(load().eiger_join_wide_workspace(nb, np_, dtype, ctypes.byref(b) if b is not None else None,
+                                            ctypes.byref(p) if p is not None else None, _variant(variant),
+                                            _mat(materialize), ctypes.byref(k) if k is not None else None,
+                                            ctypes.byref(out)))
+    return out.value
+
+
+def join_wide_into(build_keys, probe_keys, build_cols, probe_cols, build_out, probe_out, *, variant="auto",
+                   materialize="auto", knobs: Plan | None = None, out_bidx=None, out_pidx=None,
+                   capacity: int = 0, workspace: torch.Tensor, stream=None):
+    """eiger_join_wide into caller-allocated device outputs (one output tensor
+    per payload column). Returns (status, count, plan)."""
+    lib = load()
+    dt = _dtype_code(build_keys)
+    b, p = _columns(list(build_cols), build_out), _columns(list(probe_cols), probe_out)
+    cnt = ctypes.c_int64(0)
+    used = PlanT()
+    k = knobs.to_c() if knobs is not None else None
+    st = lib.eiger_join_wide(dt, _ptr(build_keys), build_keys.numel(), ctypes.byref(b) if b is not None else None,
+                             _ptr(probe_keys), probe_keys.numel(), ctypes.byref(p) if p is not None else None,
+                             _variant(variant), _mat(materialize), ctypes.byref(k) if k is not None else None,
+                             _ptr(out_bidx), _ptr(out_pidx), capacity, ctypes.byref(cnt), _ptr(workspace),
+                             workspace.numel() if workspace is not None else 0, ctypes.byref(used),
+                             _stream(stream))
+    return st, cnt.value, Plan.from_c(used)
+
+
+@dataclass
+class WideResult:
+    count: int
+    build_idx: torch.Tensor | None
+    probe_idx: torch.Tensor | None
+    build_cols: list
+    probe_cols: list
+    plan: Plan
+
+
+def join_wide(build_keys, probe_keys, build_cols=(), probe_cols=(), *, variant="auto", materialize="auto",
+              knobs: Plan | None = None, indices: bool = True, capacity: int | None = None,
+              workspace: torch.Tensor | None = None, stream=None) -> WideResult:
+    """eiger_join_wide: every match with its build and probe payload columns
+    (and the tuple IDs when ``indices``). Host inputs are copied to the GPU.
+    Retries once with the exact capacity when the first guess is too small."""
+    dev = torch.device("cuda")
+    bk, pk = _dev(build_keys, dev), _dev(probe_keys, dev)
+    bc = [_dev(t, dev) for t in build_cols]
+    pc = [_dev(t, dev) for t in probe_cols]
+    dt = _dtype_code(bk)
+    if workspace is None:
+        workspace = torch.empty(join_wide_workspace(bk.numel(), pk.numel(), dt, bc, pc, variant, materialize,
+                                                    knobs), dtype=torch.uint8, device=dev)
+    cap = pk.numel() if capacity is None else capacity
+    for attempt in range(2):
+        c = max(cap, 1)
+        ob = torch.empty(c, dtype=torch.int32, device=dev) if indices else None
+        op = torch.empty(c, dtype=torch.int32, device=dev) if indices else None
+        bo = [torch.empty(c, dtype=t.dtype, device=dev) for t in bc]
+        po = [torch.empty(c, dtype=t.dtype, device=dev) for t in pc]
+        st, n, used = join_wide_into(bk, pk, bc, pc, bo, po, variant=variant, materialize=materialize,
+                                     knobs=knobs, out_bidx=ob, out_pidx=op, capacity=cap, workspace=workspace,
+                                     stream=stream)
+        if st == ERR_CAPACITY and attempt == 0:
+            cap = n
+            continue
+        _check(st)
+        break
+    cut = lambda t: None if t is None else t[:n]
+    return WideResult(n, cut(ob), cut(op), [t[:n] for t in bo], [t[:n] for t in po], used)
+
+
+def _aggs(aggs, outs=None) -> AggsT:
+    """eiger_aggs from a list of (op, values tensor or None for count)."""
+    if len(aggs) > MAX_AGGS:
+        raise ValueError(f"at most {MAX_AGGS} aggregates")
+    a = AggsT()
+    a.n = len(aggs)
+    for q, (op, vals) in enumerate(aggs):
+        a.op[q] = AGG_OPS[op] if isinstance(op, str) else int(op)
+        a.bytes[q] = vals.element_size() if vals is not None else 8
+        a.vals[q] = vals.data_ptr() if vals is not None and vals.numel() else None
+        if outs is not None:
+            a.out[q] = outs[q].data_ptr() if outs[q].numel() else None
+    return a
+
+
+def _gb_variant(v) -> int:
+    return GB_VARIANTS[v] if isinstance(v, str) else int(v)
+
+
+def groupby_workspace(n: int, dtype: int, aggs, variant="auto") -> int:
+    out = ctypes.c_size_t(0)
+    a = _aggs(list(aggs))
+    _check(load().eiger_groupby_workspace(n, dtype, ctypes.byref(a), _gb_variant(variant), ctypes.byref(out)))
+    return out.value
+
+
+def groupby_into(keys, aggs, out_keys, outs, *, variant="auto", knobs: GbPlan | None = None, capacity: int = 0,
+                 workspace: torch.Tensor, stream=None):
+    """eiger_groupby into caller-allocated outputs. Returns (status, groups, plan)."""
+    lib = load()
+    a = _aggs(list(aggs), outs)
+    cnt = ctypes.c_int64(0)
+    used = GbPlanT()
+    k = knobs.to_c() if knobs is not None else None
+    st = lib.eiger_groupby(_dtype_code(keys), _ptr(keys), keys.numel(), ctypes.byref(a), _gb_variant(variant),
+                           ctypes.byref(k) if k is not None else None, _ptr(out_keys), capacity, ctypes.byref(cnt),
+                           _ptr(workspace), workspace.numel() if workspace is not None else 0, ctypes.byref(used),
+                           _stream(stream))
+    return st, cnt.value, GbPlan.from_c(used)
+
+
+@dataclass
+class GroupByResult:
+    groups: int
+    keys: torch.Tensor
+    aggs: list
+    plan: GbPlan
+
+
+def groupby(keys, aggs=(), *, variant="auto", knobs: GbPlan | None = None, capacity: int | None = None,
+            workspace: torch.Tensor | None = None, stream=None) -> GroupByResult:
+    """eiger_groupby: every distinct key with its aggregates (int64 each).
+    ``aggs``: list of (op, values) with op in sum/count/min/max (values None
+    for count). Host inputs are copied to the GPU. Retries once with the exact
+    capacity when the first guess is too small."""
+    dev = torch.device("cuda")
+    k = _dev(keys, dev)
+    ag = [(op, _dev(v, dev)) for op, v in aggs]
+    dt = _dtype_code(k)
+    if workspace is None:
+        workspace = torch.empty(groupby_workspace(k.numel(), dt, ag, variant), dtype=torch.uint8, device=dev)
+    cap = min(k.numel(), 1 << 20) if capacity is None else capacity
+    for attempt in range(2):
+        c = max(cap, 1)
+        ok = torch.empty(c, dtype=k.dtype, device=dev)
+        outs = [torch.empty(c, dtype=torch.int64, device=dev) for _ in ag]
+        st, n, used = groupby_into(k, ag, ok, outs, variant=variant, knobs=knobs, capacity=cap, workspace=workspace,
+                                   stream=stream)
+        if st == ERR_CAPACITY and attempt == 0:
+            cap = n
+            continue
+        _check(st)
+        break
+    return GroupByResult(n, ok[:n], [o[:n] for o in outs], used)
+
+
 def join_static_noalloc_into(build_keys, probe_keys, out_bidx, out_pidx, capacity: int,
                              stream=None):
     """eiger_join_static_noalloc into caller-owned outputs: the static join
@@ -511,8 +750,9 @@ def mlp_forward(params: torch.Tensor, x: torch.Tensor, stream=None) -> torch.Ten
     return z
 
 
-def mlp_grad(params, x, cost, workspace=None, stream=None):
-    """(mean expected regret, gradient) from the library's gradient kernels."""
+def mlp_grad(params, x, cost, tau: float = 0.0, workspace=None, stream=None):
+    """(mean loss, gradient) from the library's gradient kernels: the expected
+    regret for tau = 0, the soft-target cross-entropy for tau > 0."""
     lib = load()
     n = x.shape[0]
     if workspace is None:
@@ -521,7 +761,7 @@ def mlp_grad(params, x, cost, workspace=None, stream=None):
         workspace = torch.empty(max(b.value, 1), dtype=torch.uint8, device=x.device)
     g = torch.empty_like(params)
     L = torch.empty(1, dtype=torch.float32, device=x.device)
-    _check(lib.eiger_mlp_grad(_ptr(params), _ptr(x), _ptr(cost), n, _ptr(g), _ptr(L), _ptr(workspace),
+    _check(lib.eiger_mlp_grad(_ptr(params), _ptr(x), _ptr(cost), n, tau, _ptr(g), _ptr(L), _ptr(workspace),
                               workspace.numel(), _stream(stream)))
     return L, g
 

@@ -4,9 +4,10 @@ The paper chooses join algorithms and knobs at run time from cheap statistics
 (Sec. 1, Table 1, Sec. 4). Here that choice is learned: every seeded synthetic
 join is timed under each of the 15 plan classes (eiger_class_plan), and a
 small network (the library's FP32 kernels, eiger_mlp_*) is trained on the 12
-runtime features (eiger_features) to minimise the expected regret of its
-choice. The exhaustive choice (fastest measured class) is the judge; the
-rule-based selector (eiger_plan) is the fallback and the comparison.
+runtime features (eiger_features) toward the classes near the fastest (a
+soft-target cross-entropy over the measured slowdowns). The exhaustive
+choice (fastest measured class) is the judge; the rule-based selector
+(eiger_plan) is the fallback and the comparison.
 
 Pipeline (all steps on the GPU, each writes plain text under selector_data/):
   sweep(...)  -> timings.csv (one row per join; resumable, append-only)
@@ -251,10 +252,17 @@ def init_params(seed: int = 0) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
+TAU = 0.05  # temperature of the soft target softmax(-slowdown / TAU)
+
+
 def train(X: np.ndarray, T: np.ndarray, steps: int = 4000, lr: float = 2e-3, seed: int = 0,
-          n_train: int = 2500):
+          n_train: int = 2500, tau: float = TAU):
     """Full-batch Adam on the training joins with the library's gradient and
-    optimiser kernels. Returns the model dict (see save_model)."""
+    optimiser kernels. The loss is the cross-entropy toward the soft target
+    softmax(-slowdown / tau): every class within a few tau of the fastest
+    shares the target, so near-ties cost little, and unlike the expected
+    regret (tau = 0) the loss does not flatten once a class dominates the
+    softmax. Returns the model dict (see save_model)."""
     tr, _ = split(len(X), n_train)
     mean = X[tr].mean(axis=0)
     scale = np.maximum(X[tr].std(axis=0), 1e-3)
@@ -266,12 +274,12 @@ def train(X: np.ndarray, T: np.ndarray, steps: int = 4000, lr: float = 2e-3, see
     ws = None
     hist = []
     for step in range(1, steps + 1):
-        L, g = eiger.mlp_grad(p, x, c, workspace=ws)
+        L, g = eiger.mlp_grad(p, x, c, tau, workspace=ws)
         eiger.mlp_adam(p, g, m, v, step, lr)
         if step % 200 == 0 or step == 1:
             hist.append((step, float(L)))
     return {"params": p.cpu().numpy().tolist(), "mean": mean.tolist(), "scale": scale.tolist(),
-            "n_train": int(len(tr)), "steps": steps, "lr": lr, "seed": seed, "loss_history": hist}
+            "n_train": int(len(tr)), "steps": steps, "lr": lr, "seed": seed, "tau": tau, "loss_history": hist}
 
 
 def predict(model: dict, X: np.ndarray) -> np.ndarray:

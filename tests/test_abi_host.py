@@ -173,3 +173,52 @@ def test_batched_workspace_query_needs_no_gpu(lib):
     assert lib.load().eiger_join_batched_workspace(descs, 3, lib.I32, ctypes.byref(bad), ctypes.byref(ws)) == lib.ERR_INVALID_ARG
     st = ctypes.c_int32(0)
     assert lib.load().eiger_join_batched(lib.I32, None, 3, None, None, None, None, 0, None) == lib.ERR_INVALID_ARG
+
+
+def test_wide_workspace_counts_carried_columns(lib):
+    """GFTR carries the payload columns through the passes, so its workspace
+    grows by two copies of every column; GFUR's does not."""
+    import torch
+
+    nb, np_ = 1 << 20, 1 << 22
+    bcols = [torch.empty(0, dtype=torch.int64), torch.empty(0, dtype=torch.int32)]
+    pcols = [torch.empty(0, dtype=torch.int64)]
+    knobs = lib.Plan("phj2", 5, 5, 1)
+    gfur = lib.join_wide_workspace(nb, np_, lib.I64, bcols, pcols, "phj2", "gfur", knobs)
+    gftr = lib.join_wide_workspace(nb, np_, lib.I64, bcols, pcols, "phj2", "gftr", knobs)
+    assert gftr - gfur >= 2 * (nb * 12 + np_ * 8)
+    smj = lib.join_wide_workspace(nb, np_, lib.I64, bcols, pcols, "smj", "gftr", None)
+    assert smj >= 2 * (nb * 12 + np_ * 8)
+    assert lib.join_wide_workspace(nb, np_, lib.I64, [], [], "smj", "gfur", None) == \
+        lib.join_workspace(nb, np_, lib.I64, "smj")
+
+
+def test_wide_argument_checks(lib):
+    so = lib.load()
+    ws = ctypes.c_size_t(0)
+    bad = lib.ColumnsT()
+    bad.n = 5
+    assert so.eiger_join_wide_workspace(10, 10, lib.I64, ctypes.byref(bad), None, lib.PHJ2, lib.GFTR, None,
+                                        ctypes.byref(ws)) == lib.ERR_INVALID_ARG
+    bad.n = 1
+    bad.bytes[0] = 2
+    assert so.eiger_join_wide_workspace(10, 10, lib.I64, ctypes.byref(bad), None, lib.PHJ2, lib.GFTR, None,
+                                        ctypes.byref(ws)) == lib.ERR_INVALID_ARG
+    assert "bytes" in lib.last_error()
+    assert so.eiger_join_wide_workspace(10, 10, lib.I64, None, None, lib.SMJ, 7, None,
+                                        ctypes.byref(ws)) == lib.ERR_INVALID_ARG
+    ok = lib.ColumnsT()
+    ok.n = 1
+    ok.bytes[0] = 8
+    cnt = ctypes.c_int64(0)
+    # data pointers are required by the join itself
+    assert so.eiger_join_wide(lib.I64, None, 0, ctypes.byref(ok), None, 0, None, lib.SMJ, lib.GFTR, None,
+                              None, None, 0, ctypes.byref(cnt), None, 0, None, None) == lib.ERR_INVALID_ARG
+
+
+def test_smj_knob_validation(lib):
+    so = lib.load()
+    ws = ctypes.c_size_t(0)
+    k = lib.Plan("smj", 9, 0, 1).to_c()
+    assert so.eiger_join_workspace(100, 100, lib.I64, lib.SMJ, ctypes.byref(k), ctypes.byref(ws)) == 0
+    assert so.eiger_join_workspace(100, 100, lib.I64, 6, None, ctypes.byref(ws)) == lib.ERR_INVALID_ARG

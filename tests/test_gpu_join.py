@@ -142,6 +142,8 @@ PLANS = [
     ("phj2", {"bits1": 2, "bits2": 3}),
     ("phj2", {"bits1": 7, "bits2": 5}),
     ("phj2", {"bits1": 12, "bits2": 8}),
+    ("smj", {}),
+    ("smj", {"bits1": 3}),
 ]
 
 
@@ -153,7 +155,7 @@ def test_join_parity(eiger, oracle_mod, case, variant, kw):
     _run(eiger, oracle_mod, bk, pk, variant, _knobs(eiger, variant, bk, **kw))
 
 
-@pytest.mark.parametrize("variant", ["static", "auto", "nphj", "phj1", "phj2"])
+@pytest.mark.parametrize("variant", ["static", "auto", "nphj", "phj1", "phj2", "smj"])
 @pytest.mark.parametrize("nb,np_", [(0, 0), (0, 10), (10, 0), (1, 1), (1, 5000), (4097, 8193),
                                     (4096, 4096)])
 def test_join_small_and_empty(eiger, oracle_mod, variant, nb, np_):
@@ -165,10 +167,12 @@ def test_join_small_and_empty(eiger, oracle_mod, variant, nb, np_):
 
 
 @pytest.mark.parametrize("variant,kw", [("nphj", {}), ("phj1", {"bits1": 3}),
-                                        ("phj2", {"bits1": 2, "bits2": 2}), ("static", {})])
+                                        ("phj2", {"bits1": 2, "bits2": 2}), ("static", {}), ("smj", {})])
 def test_join_single_key_many_duplicates(eiger, oracle_mod, variant, kw):
     """10,000 equal build keys: one build partition spans three shared-memory
-    tables, and every probe row yields 10,000 matches (stage spill path)."""
+    tables, and every probe row yields 10,000 matches (stage spill path; for
+    the sort-merge join a build window of three staged segments and the
+    load-balanced expansion)."""
     bk = np.full(10_000, 77, I64)
     pk = np.array([77, 5, 77, 77, 78] * 3, I64)
     _run(eiger, oracle_mod, bk, pk, variant, _knobs(eiger, variant, bk, **kw))
@@ -177,7 +181,7 @@ def test_join_single_key_many_duplicates(eiger, oracle_mod, variant, kw):
 def test_join_probe_outside_build_range(eiger, oracle_mod):
     bk = np.arange(1000, 2000, dtype=I64)
     pk = np.concatenate([np.arange(0, 1000), np.arange(2000, 3000)]).astype(I64)
-    for v in ("auto", "phj2", "static"):
+    for v in ("auto", "phj2", "static", "smj"):
         r = _run(eiger, oracle_mod, bk, pk, v, _knobs(eiger, v, bk, bits1=3, bits2=3) if v == "phj2" else None)
         assert r.count == 0
 
@@ -216,7 +220,7 @@ def test_payload_materialisation(eiger, oracle_mod):
     bk, pk = _dup_heavy_i64(rng, 2000, 3000)
     bp = rng.integers(-2**62, 2**62, size=bk.size).astype(np.int64)
     pp = rng.integers(-2**62, 2**62, size=pk.size).astype(np.int64)
-    for v, kn in (("nphj", None), ("phj2", eiger.Plan("phj2", 3, 2, 1)), ("static", None)):
+    for v, kn in (("nphj", None), ("phj2", eiger.Plan("phj2", 3, 2, 1)), ("static", None), ("smj", None)):
         r = eiger.join(torch.from_numpy(bk).cuda(), torch.from_numpy(pk).cuda(),
                        build_pay=torch.from_numpy(bp).cuda(), probe_pay=torch.from_numpy(pp).cuda(),
                        variant=v, knobs=kn, payloads=True)
@@ -228,7 +232,8 @@ def test_payload_materialisation(eiger, oracle_mod):
 
 
 @pytest.mark.parametrize("variant,kn", [("auto", None), ("nphj", None), ("static", None),
-                                        ("phj1", ("phj1", 5, 0, 1)), ("phj2", ("phj2", 4, 4, 1))])
+                                        ("phj1", ("phj1", 5, 0, 1)), ("phj2", ("phj2", 4, 4, 1)),
+                                        ("smj", None), ("smj", ("smj", 5, 0, 1))])
 def test_join_sum_parity(eiger, oracle_mod, variant, kn):
     rng = np.random.default_rng(31)
     n_dim, n_fact = 30_000, 200_000

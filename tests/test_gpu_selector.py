@@ -40,12 +40,12 @@ def test_forward_matches_oracle(eiger, n):
     np.testing.assert_allclose(z, zo, rtol=1e-4, atol=1e-4 * np.abs(zo).max())
 
 
-@pytest.mark.parametrize("n", [3, 257, 2500])
-def test_gradient_matches_oracle(eiger, n):
+@pytest.mark.parametrize("n,tau", [(3, 0.0), (257, 0.0), (2500, 0.0), (3, 0.05), (257, 0.05), (2500, 0.5)])
+def test_gradient_matches_oracle(eiger, n, tau):
     params, X, C = _problem(100 + n, n)
     L, g = eiger.mlp_grad(torch.from_numpy(params).cuda(), torch.from_numpy(X).cuda(),
-                          torch.from_numpy(C).cuda())
-    Lo, go = mlp.loss_and_grad(params.astype(np.float64), X.astype(np.float64), C.astype(np.float64))
+                          torch.from_numpy(C).cuda(), tau)
+    Lo, go = mlp.loss_and_grad(params.astype(np.float64), X.astype(np.float64), C.astype(np.float64), tau)
     g = g.cpu().numpy()
     assert float(L) == pytest.approx(Lo, rel=1e-5)
     # relative error of the whole gradient vector, and per component

@@ -21,18 +21,49 @@ def test_parameter_count():
     assert mlp.P == 64 * 12 + 64 + 64 * 64 + 64 + 15 * 64 + 15 == 5967
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_gradient_matches_central_differences(seed):
+@pytest.mark.parametrize("seed,tau", [(0, 0.0), (1, 0.0), (2, 0.0), (3, 0.05), (4, 0.5)])
+def test_gradient_matches_central_differences(seed, tau):
     params, X, C = _random(seed)
-    _, g = mlp.loss_and_grad(params, X, C)
+    _, g = mlp.loss_and_grad(params, X, C, tau)
     rng = np.random.default_rng(100 + seed)
     idx = rng.choice(mlp.P, size=300, replace=False)
     h = 1e-6
     for q in idx:
         e = np.zeros(mlp.P)
         e[q] = h
-        num = (mlp.loss(params + e, X, C) - mlp.loss(params - e, X, C)) / (2 * h)
+        num = (mlp.loss(params + e, X, C, tau) - mlp.loss(params - e, X, C, tau)) / (2 * h)
         assert num == pytest.approx(g[q], rel=1e-5, abs=1e-9)
+
+
+def test_cross_entropy_of_uniform_logits_is_log_classes():
+    """Equal logits give p = 1/15 whatever the target, so -sum q log p = ln 15."""
+    _, X, C = _random(7)
+    assert mlp.loss(np.zeros(mlp.P), X, C, 0.05) == pytest.approx(np.log(15.0), rel=1e-12)
+
+
+def test_cross_entropy_sharp_target_is_negative_log_likelihood():
+    """With one class 1+ cheaper than every other and tau = 1e-3, the soft
+    target is one-hot up to exp(-1000): the loss is -log p of that class."""
+    params, X, C = _random(8)
+    best = np.argmin(C, axis=1)
+    C = C + 1.0
+    C[np.arange(len(C)), best] = 0.0
+    z, _ = mlp.forward(params, X)
+    zs = z - z.max(axis=1, keepdims=True)
+    nll = -(zs[np.arange(len(z)), best] - np.log(np.exp(zs).sum(axis=1)))
+    assert mlp.loss(params, X, C, 1e-3) == pytest.approx(nll.mean(), rel=1e-12)
+
+
+def test_cross_entropy_splits_ties_evenly():
+    """Two zero-cost classes and the rest far more expensive: the target puts
+    one half on each tie, so the loss of a network that does the same is ln 2."""
+    d = {name: np.zeros(shape) for name, shape in mlp.SHAPES}
+    d["b3"] = np.full(mlp.OUT, -1e3)
+    d["b3"][[2, 9]] = 0.0
+    C = np.full((3, mlp.OUT), 50.0)
+    C[:, [2, 9]] = 0.0
+    X = np.random.default_rng(9).normal(size=(3, mlp.IN))
+    assert mlp.loss(mlp.pack(d), X, C, 0.1) == pytest.approx(np.log(2.0), rel=1e-9)
 
 
 def test_constant_logits_closed_form():

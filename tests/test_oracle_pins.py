@@ -272,3 +272,19 @@ def test_exact_ndv_matches_set(oracle_mod):
         k = rng.integers(-50, 50, size=3000).astype(dtype)
         assert oracle_mod.exact_ndv(k) == len(set(k.tolist()))
     assert oracle_mod.exact_ndv(np.empty(0, np.int64)) == 0
+
+
+def test_wide_join_matches_nested_loop_with_columns(oracle_mod):
+    """Every (i, j) with equal keys, found by a nested loop, carries row i of
+    each build column and row j of each probe column."""
+    rng = np.random.default_rng(77)
+    bk = rng.integers(-5, 6, size=40).astype(np.int64)
+    pk = rng.integers(-7, 8, size=60).astype(np.int64)
+    bc = [rng.integers(-2**62, 2**62, size=40), rng.integers(-2**31, 2**31, size=40).astype(np.int32)]
+    pc = [rng.integers(0, 1000, size=60).astype(np.int32)]
+    want = sorted((j, i, tuple(int(c[i]) for c in bc), tuple(int(c[j]) for c in pc))
+                  for j in range(60) for i in range(40) if bk[i] == pk[j])
+    b, p, obc, opc = oracle_mod.join_wide(bk, pk, bc, pc)
+    got = [(int(p[k]), int(b[k]), tuple(int(c[k]) for c in obc), tuple(int(c[k]) for c in opc))
+           for k in range(len(b))]
+    assert got == want
