@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(kGbThreads)
     gb_hash_global_kernel(const InKey* __restrict__ keys, uint32_t n, uint64_t offset, GbTable<KeyT> t, AggSpec s,
                           unsigned* err) {
     const unsigned long long total = t.slots + 1;
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    for (unsigned long long rr = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; rr < n;
+         rr += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t r = (uint32_t)rr;
         const KeyT k = KeyCodec<KeyT>::encode((int64_t)__ldcs(keys + r), offset);
         const unsigned long long slot = gb_global_slot(t, k, err);
         if (slot == ~0ull) continue;
@@ -243,13 +245,14 @@ __global__ void __launch_bounds__(kGbThreads)
     __syncthreads();
     long long* scratch = s_scratch + (threadIdx.x & ~(kWarp - 1));
     // contiguous row range per CTA, rounds of blockDim rows
-    const uint32_t per = (uint32_t)(((unsigned long long)n + gridDim.x - 1) / gridDim.x);
-    const uint32_t lo = blockIdx.x * per;
-    const uint32_t hi = lo + per < n ? lo + per : n;
+    const unsigned long long per = ((unsigned long long)n + gridDim.x - 1) / gridDim.x;
+    const unsigned long long lo64 = blockIdx.x * per;
+    const uint32_t lo = (uint32_t)(lo64 < n ? lo64 : n);
+    const uint32_t hi = (uint32_t)(lo64 + per < n ? lo64 + per : n);
     bool full = false;
-    for (uint32_t base = lo; base < hi; base += kGbThreads) {
-        const uint32_t r = base + threadIdx.x;
-        bool ok = r < hi;
+    for (unsigned long long base = lo; base < hi; base += kGbThreads) {
+        const uint32_t r = (uint32_t)(base + threadIdx.x);
+        bool ok = base + threadIdx.x < hi;
         uint32_t slot = 0;
         if (ok) {
             const KeyT k = KeyCodec<KeyT>::encode((int64_t)__ldcs(keys + r), offset);
@@ -367,9 +370,9 @@ __global__ void __launch_bounds__(kGbThreads)
         const unsigned long long p = s_item;
         if (p >= a.P) break;
         const uint32_t beg = a.start[p], end = a.start[p + 1];
-        for (uint32_t base = beg; base < end; base += kGbThreads) {
-            const uint32_t r = base + threadIdx.x;
-            bool ok = r < end;
+        for (unsigned long long base = beg; base < end; base += kGbThreads) {
+            const uint32_t r = (uint32_t)(base + threadIdx.x);
+            bool ok = base + threadIdx.x < end;
             uint32_t slot = 0;
             if (ok) {
                 slot = tab.slot_of(__ldcs(a.key + r));
@@ -543,6 +546,7 @@ cudaError_t gb_part_run(const GbArgs& g, const GbPlanDev& plan, const GbScratch&
 }  // namespace
 
 size_t gb_smem_table_bytes(unsigned long long slots, int naggs, bool key32) {
+    if (slots > (1ull << 16)) return ~(size_t)0;  // far beyond any shared-memory budget
     return key32 ? smem_gb_bytes<uint32_t>((uint32_t)slots, naggs) : smem_gb_bytes<uint64_t>((uint32_t)slots, naggs);
 }
 

@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kSmjThreads, 2) smj_join_kernel(SmjIn<KeyT> a,
             s_pid[i] = POS ? s0 + i : __ldcs(a.pidx + s0 + i);
         }
         const uint32_t wlo = a.window[2 * c], whi = a.window[2 * c + 1];
-        for (uint32_t seg = wlo; seg < whi; seg += kSmjWin) {
+        for (unsigned long long seg64 = wlo; seg64 < whi; seg64 += kSmjWin) {
+            const uint32_t seg = (uint32_t)seg64;
             const uint32_t bn = whi - seg < kSmjWin ? whi - seg : kSmjWin;
             __syncthreads();  // previous segment consumed; chunk staged
             for (uint32_t i = threadIdx.x; i < bn; i += kSmjThreads) {
