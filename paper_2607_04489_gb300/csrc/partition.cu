@@ -111,8 +111,11 @@ __device__ __forceinline__ uint32_t digit_of(KeyT k, int dshift, uint32_t dmask)
 }
 
 // Exclusive scan of in[0, n) into out[0, n), n <= kPartItems * blockDim.x.
-// Block-collective; returns the total. s_warp: blockDim.x / 32 words.
-__device__ uint32_t block_scan_smem(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* s_warp) {
+// Block-collective; returns the total. s_warp: blockDim.x / 32 words. With
+// `rebase`, also rebase[i] -= out[i] for every i (by the thread that wrote
+// out[i], so no barrier is needed in between).
+__device__ uint32_t block_scan_smem(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* s_warp,
+                                    uint32_t* rebase = nullptr) {
     const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
     uint32_t beg = threadIdx.x * per;
     if (beg > n) beg = n;
@@ -146,6 +149,7 @@ __device__ uint32_t block_scan_smem(const uint32_t* in, uint32_t* out, uint32_t 
     const uint32_t total = s_warp[nw - 1];
     for (uint32_t i = beg; i < end; ++i) {
         out[i] = prefix;
+        if (rebase) rebase[i] -= prefix;
         prefix += in[i];
     }
     return total;
@@ -180,30 +184,33 @@ struct TileRing {
             return a.in_key + start;
     }
 
-    // Warp 0 only: start loading tile t into buffer b. The lanes copy the few
-    // unaligned head/tail elements in parallel; lane 0 then arrives on the
-    // buffer's barrier with the bulk byte count and issues the bulk copies.
-    __device__ void issue(const PartPass<InKey, KeyT>& a, uint32_t t, int b) const {
+    // Warp 0 only: start loading tile `tl` into buffer b (with its tuple IDs
+    // when ROWS). Lane 0 declares the bulk bytes on the buffer's barrier and
+    // issues the bulk copies first; the lanes then copy the few unaligned
+    // head and tail elements in parallel while the bulk copies are in flight,
+    // and lane 0 arrives once they are written, so waiters see both.
+    template <bool ROWS>
+    __device__ void issue(const PartPass<InKey, KeyT>& a, const Tile& tl, int b) const {
         const unsigned lane = lane_id();
-        const Tile tl = get_tile(a, t);
         const E* kf = key_src(a, tl.start);
         uint32_t klead, klo, khi;
         uint32_t bytes = tile_copy_plan(kf, tl.len, klead, klo, khi);
-        edges_warp(keys(b), kf, tl.len, klead, klo, khi, lane);
         uint32_t ilead = 0, ilo = 0, ihi = 0;
         const uint32_t* rf = nullptr;
-        if constexpr (!FIRST) {
+        if constexpr (ROWS) {
             rf = a.in_idx + tl.start;
             bytes += tile_copy_plan(rf, tl.len, ilead, ilo, ihi);
-            edges_warp(rows(b), rf, tl.len, ilead, ilo, ihi, lane);
         }
-        __syncwarp();
         if (lane == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bar[b], bytes);
+            mbar_expect_tx(&bar[b], bytes);
             tile_copy_body(keys(b), kf, klead, klo, khi, &bar[b]);
-            if constexpr (!FIRST) tile_copy_body(rows(b), rf, ilead, ilo, ihi, &bar[b]);
+            if constexpr (ROWS) tile_copy_body(rows(b), rf, ilead, ilo, ihi, &bar[b]);
         }
+        edges_warp(keys(b), kf, tl.len, klead, klo, khi, lane);
+        if constexpr (ROWS) edges_warp(rows(b), rf, tl.len, ilead, ilo, ihi, lane);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar[b]);
     }
 
     // Lane l of the issuing warp copies head element l and tail element l.
@@ -278,18 +285,25 @@ __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey,
     __syncthreads();
     const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
     uint32_t t = blockIdx.x;
-    if (threadIdx.x < kWarp && t < ntiles) ring.issue(a, t, 0);
+    Tile d_next{};  // warp 0: descriptor of the next tile to issue, loaded one tile early
+    if (threadIdx.x < kWarp) {
+        if (t < ntiles) ring.template issue<false>(a, get_tile(a, t), 0);
+        if (t + gridDim.x < ntiles) d_next = get_tile(a, t + gridDim.x);
+    }
     for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
         const int b = it & 1;
         const uint32_t tn = t + gridDim.x;
-        if (threadIdx.x < kWarp && tn < ntiles) ring.issue(a, tn, b ^ 1);
+        if (threadIdx.x < kWarp && tn < ntiles) {
+            ring.template issue<false>(a, d_next, b ^ 1);
+            if (tn + gridDim.x < ntiles) d_next = get_tile(a, tn + gridDim.x);
+        }
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
+        const Tile tl = get_tile(a, t);
         const bool ok = mbar_wait(&ring.bar[b], (it >> 1) & 1);
         if (__syncthreads_or(!ok)) {
             ring_abort(ring, b ^ 1, ((it + 1) >> 1) & 1, tn < ntiles, err);
             return;
         }
-        const Tile tl = get_tile(a, t);
         const auto* kbuf = ring.keys(b) + lead_of(Ring::key_src(a, tl.start));
 #pragma unroll 4
         for (uint32_t e = threadIdx.x; e < tl.len; e += kPartThreads) {
@@ -350,7 +364,7 @@ __device__ __forceinline__ void carry_column(const V* __restrict__ src, V* __res
     __syncthreads();
     for (uint32_t q = threadIdx.x; q < nk; q += blockDim.x) {
         const uint32_t d = s_dig[q];
-        dst[s_goff[d] + (q - s_start[d])] = s_col[q];
+        dst[s_goff[d] + q] = s_col[q];
     }
     __syncthreads();
 }
@@ -395,21 +409,28 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
     uint32_t t = blockIdx.x;
     // Global offsets of this CTA's first tile; later ones are loaded one tile
     // ahead into registers (thread i owns digits i, i + blockDim, ...).
-    uint32_t goff[kGoffPerThread];
+    uint32_t goff[kGoffPerThread] = {};
     Tile tl_cur;
     if (t < ntiles) {
         tl_cur = get_tile(a, t);
 #pragma unroll
         for (int q = 0; q < kGoffPerThread; ++q) {
             const uint32_t d = threadIdx.x + q * kPartThreads;
-            goff[q] = d < nd ? a.counts[count_index(tl_cur, t, d, a.bits)] : 0u;
+            if (d < nd) goff[q] = a.counts[count_index(tl_cur, t, d, a.bits)];
         }
     }
-    if (threadIdx.x < kWarp && t < ntiles) ring.issue(a, t, 0);
+    Tile d_next{};  // warp 0: descriptor of the next tile to issue, loaded one tile early
+    if (threadIdx.x < kWarp) {
+        if (t < ntiles) ring.template issue<!FIRST>(a, tl_cur, 0);
+        if (t + gridDim.x < ntiles) d_next = get_tile(a, t + gridDim.x);
+    }
     for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
         const int b = it & 1;
         const uint32_t tn = t + gridDim.x;
-        if (threadIdx.x < kWarp && tn < ntiles) ring.issue(a, tn, b ^ 1);
+        if (threadIdx.x < kWarp && tn < ntiles) {
+            ring.template issue<!FIRST>(a, d_next, b ^ 1);
+            if (tn + gridDim.x < ntiles) d_next = get_tile(a, tn + gridDim.x);
+        }
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
 #pragma unroll
         for (int q = 0; q < kGoffPerThread; ++q) {
@@ -427,7 +448,7 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
 #pragma unroll
             for (int q = 0; q < kGoffPerThread; ++q) {
                 const uint32_t d = threadIdx.x + q * kPartThreads;
-                goff[q] = d < nd ? a.counts[count_index(tl_cur, tn, d, a.bits)] : 0u;
+                if (d < nd) goff[q] = a.counts[count_index(tl_cur, tn, d, a.bits)];
             }
         }
         const auto* kbuf = ring.keys(b) + lead_of(Ring::key_src(a, tl.start));
@@ -448,7 +469,8 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
             if (dr[j] != kNoDigit) dr[j] |= atomicAdd(&s_cnt[dr[j]], 1u) << 12;
         __syncthreads();
 
-        const uint32_t kept = block_scan_smem(s_cnt, s_start, nd, s_warp);
+        // s_goff becomes (global offset - tile offset) of each digit
+        const uint32_t kept = block_scan_smem(s_cnt, s_start, nd, s_warp, s_goff);
         if (threadIdx.x == 0) s_kept = kept;
         __syncthreads();
 
@@ -471,7 +493,7 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
         const uint32_t nk = s_kept;
         for (uint32_t pos = threadIdx.x; pos < nk; pos += blockDim.x) {
             const uint32_t d = s_dig[pos];
-            const uint32_t g = s_goff[d] + (pos - s_start[d]);
+            const uint32_t g = s_goff[d] + pos;
             a.out_key[g] = s_key[pos];
             a.out_idx[g] = s_idx[pos];
         }
@@ -522,21 +544,28 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
     const uint32_t w = threadIdx.x / kWarp;
     const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
     uint32_t t = blockIdx.x;
-    uint32_t goff[kGoffPerThread];
+    uint32_t goff[kGoffPerThread] = {};
     Tile tl_cur;
     if (t < ntiles) {
         tl_cur = get_tile(a, t);
 #pragma unroll
         for (int q = 0; q < kGoffPerThread; ++q) {
             const uint32_t d = threadIdx.x + q * kPartThreads;
-            goff[q] = d < nd ? a.counts[count_index(tl_cur, t, d, a.bits)] : 0u;
+            if (d < nd) goff[q] = a.counts[count_index(tl_cur, t, d, a.bits)];
         }
     }
-    if (threadIdx.x < kWarp && t < ntiles) ring.issue(a, t, 0);
+    Tile d_next{};  // warp 0: descriptor of the next tile to issue, loaded one tile early
+    if (threadIdx.x < kWarp) {
+        if (t < ntiles) ring.template issue<!FIRST>(a, tl_cur, 0);
+        if (t + gridDim.x < ntiles) d_next = get_tile(a, t + gridDim.x);
+    }
     for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
         const int b = it & 1;
         const uint32_t tn = t + gridDim.x;
-        if (threadIdx.x < kWarp && tn < ntiles) ring.issue(a, tn, b ^ 1);
+        if (threadIdx.x < kWarp && tn < ntiles) {
+            ring.template issue<!FIRST>(a, d_next, b ^ 1);
+            if (tn + gridDim.x < ntiles) d_next = get_tile(a, tn + gridDim.x);
+        }
         for (uint32_t d = lane; d < nd; d += kWarp) s_wc[w * nd + d] = 0;
 #pragma unroll
         for (int q = 0; q < kGoffPerThread; ++q) {
@@ -554,7 +583,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
 #pragma unroll
             for (int q = 0; q < kGoffPerThread; ++q) {
                 const uint32_t d = threadIdx.x + q * kPartThreads;
-                goff[q] = d < nd ? a.counts[count_index(tl_cur, tn, d, a.bits)] : 0u;
+                if (d < nd) goff[q] = a.counts[count_index(tl_cur, tn, d, a.bits)];
             }
         }
         const auto* kbuf = ring.keys(b) + lead_of(Ring::key_src(a, tl.start));
@@ -588,7 +617,8 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
             s_cnt[d] = run;
         }
         __syncthreads();
-        const uint32_t kept = block_scan_smem(s_cnt, s_start, nd, s_warp);
+        // s_goff becomes (global offset - tile offset) of each digit
+        const uint32_t kept = block_scan_smem(s_cnt, s_start, nd, s_warp, s_goff);
         if (threadIdx.x == 0) s_kept = kept;
         __syncthreads();
 #pragma unroll
@@ -609,7 +639,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
         const uint32_t nk = s_kept;
         for (uint32_t pos = threadIdx.x; pos < nk; pos += blockDim.x) {
             const uint32_t d = s_dig[pos];
-            const uint32_t g = s_goff[d] + (pos - s_start[d]);
+            const uint32_t g = s_goff[d] + pos;
             a.out_key[g] = s_key[pos];
             a.out_idx[g] = s_idx[pos];
         }
