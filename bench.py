@@ -109,19 +109,21 @@ def kernel_sources_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from profiles/dram_traffic.txt, or None
-    when the file is missing or was taken on other kernel sources."""
+def recorded_traffic(kernel: str, workload: str = "sweep"):
+    """DRAM bytes per launch of `kernel` in `workload` from
+    profiles/dram_traffic.txt, or None when the file is missing, has no such
+    entry, or was taken on other kernel sources."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         with open(path) as f:
             rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
     except OSError:
         return None
-    table = {r[0]: r[1] for r in rows if len(r) == 2}
-    if table.get("sources") != kernel_sources_digest() or kernel not in table:
+    digest = next((r[1] for r in rows if len(r) == 2 and r[0] == "sources"), None)
+    table = {(r[0], r[1]): r[2] for r in rows if len(r) == 3}
+    if digest != kernel_sources_digest() or (workload, kernel) not in table:
         return None
-    return float(table[kernel])
+    return float(table[(workload, kernel)])
 
 
 def measured_peaks():
@@ -195,6 +197,14 @@ class ClockSampler:
                           if r[i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "samples": len(rows),
                 "power_w_max": max(num(r[3]) for r in rows), "reasons": reasons}
+
+
+def sweep_traffic_key(args):
+    """Which recorded ncu traffic applies to this run of the sweep workload:
+    only the default sizes, keys and skew were captured."""
+    if (args.log2_nb, args.ratio, args.keys, args.theta) != (26, 4, "dense", 0.0):
+        return None
+    return {"auto": "sweep", "smj": "smj"}.get(args.variant)
 
 
 def workload_desc(args):
@@ -344,40 +354,74 @@ def run_eiger(args):
         ws = torch.empty(eiger.join_workspace(nb, np_, eiger.I64, args.variant), dtype=torch.uint8,
                          device=dev)
 
-    # ---- end to end through the public API from pinned host buffers
+    # ---- end to end through the public API from pinned host buffers. Every
+    # step copies its own keys in and its pairs out; consecutive steps are
+    # pipelined over three streams with double-buffered device arrays, as a
+    # caller streaming batches would run them: step i+1's upload and step
+    # i-1's download overlap step i's join.
     e2e = None
     if not args.no_e2e:
         hb = bk.cpu().pin_memory()
         hp = pk.cpu().pin_memory()
-        hob = torch.empty(np_, dtype=torch.int32).pin_memory()
-        hop = torch.empty(np_, dtype=torch.int32).pin_memory()
-        dbk = torch.empty_like(bk)
-        dpk = torch.empty_like(pk)
+        hob = [torch.empty(np_, dtype=torch.int32).pin_memory() for _ in range(2)]
+        hop = [torch.empty(np_, dtype=torch.int32).pin_memory() for _ in range(2)]
+        dbk = [bk, torch.empty_like(bk)]
+        dpk = [pk, torch.empty_like(pk)]
+        dob = [out_b, torch.empty_like(out_b)]
+        dop = [out_p, torch.empty_like(out_p)]
+        h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        up_done = [torch.cuda.Event() for _ in range(2)]
+        join_done = [torch.cuda.Event() for _ in range(2)]
+        down_done = [torch.cuda.Event() for _ in range(2)]
 
-        def e2e_step():
-            dbk.copy_(hb, non_blocking=True)
-            dpk.copy_(hp, non_blocking=True)
-            st, cnt, _ = eiger.join_into(dbk, dpk, variant=args.variant, out_bidx=out_b,
-                                         out_pidx=out_p, capacity=np_, workspace=ws, stream=stream)
-            if st != eiger.OK or cnt != np_:
-                raise RuntimeError(f"join failed: {eiger.last_error()}")
-            hob.copy_(out_b, non_blocking=True)
-            hop.copy_(out_p, non_blocking=True)
+        def upload(slot):
+            h2d.wait_event(join_done[slot])  # the join that last read this slot is done
+            with torch.cuda.stream(h2d):
+                dbk[slot].copy_(hb, non_blocking=True)
+                dpk[slot].copy_(hp, non_blocking=True)
+            up_done[slot].record(h2d)
 
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
+        def run_steps(n):
+            for q in range(2):
+                join_done[q].record(stream)
+                down_done[q].record(stream)
+            upload(0)
+            for i in range(n):
+                slot = i & 1
+                if i + 1 < n:
+                    upload(slot ^ 1)
+                stream.wait_event(up_done[slot])
+                stream.wait_event(down_done[slot])  # its output arrays were copied out
+                st, cnt, _ = eiger.join_into(dbk[slot], dpk[slot], variant=args.variant, out_bidx=dob[slot],
+                                             out_pidx=dop[slot], capacity=np_, workspace=ws, stream=stream)
+                if st != eiger.OK or cnt != np_:
+                    raise RuntimeError(f"join failed: {eiger.last_error()}")
+                join_done[slot].record(stream)
+                d2h.wait_event(join_done[slot])
+                with torch.cuda.stream(d2h):
+                    hob[slot].copy_(dob[slot], non_blocking=True)
+                    hop[slot].copy_(dop[slot], non_blocking=True)
+                down_done[slot].record(d2h)
+
+        run_steps(max(2, args.warmup))
         torch.cuda.synchronize(dev)
         barrier(world)
-        e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        e1.record(stream)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(h2d)
+        run_steps(args.steps)
+        for q in range(2):
+            d2h.wait_event(down_done[q])
+            d2h.wait_event(join_done[q])
+        t1.record(d2h)
         torch.cuda.synchronize(dev)
         barrier(world)
-        ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        ems = max_over_ranks(t0.elapsed_time(t1) / args.steps, world, dev)
         e2e = {"value": tuples / (ems * 1e-3), "unit": "tuples/s", "ms_per_step": ems,
                "h2d_bytes_per_step": int(bk.numel() * 8 + pk.numel() * 8),
-               "d2h_bytes_per_step": int(2 * 4 * np_)}
+               "d2h_bytes_per_step": int(2 * 4 * np_),
+               "pipelining": "upload of step i+1 and download of step i-1 overlap the join of step i"}
+        del dbk[1], dpk[1], dob[1], dop[1]
 
     # ---- roofline of the dominant stage
     peaks, peak_src = measured_peaks()
@@ -404,7 +448,8 @@ def run_eiger(args):
                  "narrow": plan.narrow, "load_factor": plan.load_factor},
         "roofline": {"bound": "hbm", "kernel": dom["stage"], "achieved": dom["gbs"], "peak": hbm,
                      "peak_source": peak_src, "unit": "GB/s", "frac": dom["gbs"] / hbm,
-                     "traffic": recorded_traffic(dom["stage"]), "algorithmic_bytes": dom["bytes"]},
+                     "traffic": recorded_traffic(dom["stage"], sweep_traffic_key(args)),
+                     "algorithmic_bytes": dom["bytes"]},
         "stages": stage_rows,
         "gpu_launches": launches,
         "static": static,
@@ -454,25 +499,29 @@ def run_batched(args):
         raise RuntimeError(f"batched join failed: status {int(bj.status)}")
     ms = e0.elapsed_time(e1) / args.steps
     # the same joins as sequential static calls, each synchronising for its count
-    seq_steps = max(1, min(args.steps, 2))
-    ws = torch.empty(max(eiger.join_workspace(b.numel(), p.numel(), eiger.I32, "static")
-                         for b, p in zip(w.builds, w.probes)), dtype=torch.uint8, device=dev)
-    def seq():
-        for j, (b, p) in enumerate(zip(w.builds, w.probes)):
-            a = int(bj.off[j])
-            st, n, _ = eiger.join_into(b, p, variant="static", out_bidx=bj.out_bidx[a:],
-                                       out_pidx=bj.out_pidx[a:], capacity=bj.capacities[j],
-                                       workspace=ws, stream=stream)
-            if st != eiger.OK:
-                raise RuntimeError(eiger.last_error())
-    seq()
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(seq_steps):
+    seq_steps = 0 if args.no_static else max(1, min(args.steps, 2))
+    sequential = None
+    if seq_steps:
+        ws = torch.empty(max(eiger.join_workspace(b.numel(), p.numel(), eiger.I32, "static")
+                             for b, p in zip(w.builds, w.probes)), dtype=torch.uint8, device=dev)
+        def seq():
+            for j, (b, p) in enumerate(zip(w.builds, w.probes)):
+                a = int(bj.off[j])
+                st, n, _ = eiger.join_into(b, p, variant="static", out_bidx=bj.out_bidx[a:],
+                                           out_pidx=bj.out_pidx[a:], capacity=bj.capacities[j],
+                                           workspace=ws, stream=stream)
+                if st != eiger.OK:
+                    raise RuntimeError(eiger.last_error())
         seq()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    sms = e0.elapsed_time(e1) / seq_steps
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(seq_steps):
+            seq()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sms = e0.elapsed_time(e1) / seq_steps
+        sequential = {"value": tuples / (sms * 1e-3), "unit": "tuples/s", "ms_per_step": sms,
+                      "speedup_of_batched": sms / ms}
     line = {"metric": METRIC, "value": tuples / (ms * 1e-3), "unit": "tuples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -480,8 +529,7 @@ def run_batched(args):
                                    "probe 4x build, per-join power-law skew U(0,1); one graph replay",
                        "joins": args.batch_joins, "tuples": tuples,
                        "knobs": vars(bj.knobs) if hasattr(bj.knobs, "__dict__") else str(bj.knobs)},
-            "sequential_static": {"value": tuples / (sms * 1e-3), "unit": "tuples/s", "ms_per_step": sms,
-                                  "speedup_of_batched": sms / ms},
+            "sequential_static": sequential,
             "gpu_launches": 4 * args.steps, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
@@ -602,7 +650,9 @@ def run_wide(args):
                      "materialize": plan.materialize},
             "roofline": {"bound": "hbm", "kernel": dom["stage"], "achieved": dom["gbs"], "peak": hbm,
                          "peak_source": peak_src, "unit": "GB/s", "frac": dom["gbs"] / hbm,
-                         "traffic": recorded_traffic(dom["stage"]), "algorithmic_bytes": dom["bytes"]},
+                         "traffic": recorded_traffic(dom["stage"], "wide" if (args.log2_nb, args.ratio,
+                                                     args.key_bytes) == (26, 4, 4) else None),
+                         "algorithmic_bytes": dom["bytes"]},
             "stages": rows, "arms": arms, "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
@@ -702,7 +752,9 @@ def run_groupby(args):
                      "table_slots": plan.table_slots, "estimate": plan.estimate},
             "roofline": {"bound": "hbm", "kernel": dom["stage"], "achieved": dom["gbs"], "peak": hbm,
                          "peak_source": peak_src, "unit": "GB/s", "frac": dom["gbs"] / hbm,
-                         "traffic": recorded_traffic(dom["stage"]), "algorithmic_bytes": dom["bytes"]},
+                         "traffic": recorded_traffic(dom["stage"], f"groupby{args.groups_log2}"
+                                                     if args.log2_rows == 28 else None),
+                         "algorithmic_bytes": dom["bytes"]},
             "stages": rows, "arms": arms, "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
