@@ -3,19 +3,23 @@
 // Each join j gets a global open-addressing multiset of slots_j = 2^ceil(log2
 // (nb_j / load)) slots in the workspace (packed 8-byte slots for int32 keys,
 // 16-byte {key, row} slots for int64 keys, the layouts of the non-partitioned
-// join). The work of all joins is cut into items of `chunk` rows: join j
-// contributes its build chunks followed by its probe chunks, and the items of
-// all joins form one sequence that a persistent grid pulls with an atomic
-// counter. A build item inserts its rows and then adds them to built[j]; a
-// probe item first waits (bounded) until built[j] == nb_j. The wait cannot
-// deadlock: items are claimed in order, every build item of join j precedes
-// its probe items, the grid is no larger than what is resident at once, and
-// build items never wait. Matches go through the CTA stage to join j's own
-// outputs, reserved on its own cursor (d_counts[j]).
+// join). Its work is cut into items: clear items (kClearSlots slots of its
+// table each), build items and probe items (`chunk` rows each). The items of
+// all joins form one sequence, pulled by a persistent grid with an atomic
+// counter, in stages: stage s holds the clear items of join s, then the build
+// items of join s-1, then the probe items of join s-2. A build item waits
+// (bounded) until all clear items of its join are done, a probe item until
+// all build rows of its join are in. So a table is cleared just before it is
+// filled (its lines are still in L2), and a join's probes start one stage
+// after its builds, with the next join's builds in between to absorb the
+// wait. No wait can deadlock: every item waits only on items earlier in the
+// sequence, items are claimed in order, waiting items never hold anything an
+// earlier item needs, and the grid is no larger than what is resident at once.
+// Matches go through the CTA stage to join j's own outputs, reserved on its
+// own cursor (d_counts[j]).
 //
-// Three launches, all asynchronous and graph-capturable: a one-block setup
-// (per-join table and item offsets by prefix sums), a table clear, and the
-// persistent join kernel.
+// Two launches, both asynchronous and graph-capturable: a one-block setup
+// (per-join tables and the stage prefix sums) and the persistent join kernel.
 #include "eiger.h"
 #include "emit.cuh"
 #include "kernels.cuh"
@@ -27,8 +31,12 @@ namespace {
 struct BatchMeta {
     unsigned long long table_off;  // first slot of the join's table
     uint32_t slots;                // power of two (0: no work)
+    uint32_t nci;                  // clear items
     uint32_t nbi;                  // build items
+    uint32_t npi;                  // probe items
 };
+
+constexpr unsigned long long kClearSlots = 16384;  // table slots per clear item
 
 struct BatchCtrl {
     unsigned long long next_item;
@@ -46,77 +54,87 @@ struct alignas(16) WideSlot {
     unsigned long long row;
 };
 
-// One block: per-join slots, items and their exclusive prefix sums.
+// One block. Pass 1: per-join slots, item counts and table offsets (prefix
+// sum of slots). Pass 2: item counts of the stages (clear items of join s,
+// build items of join s-1, probe items of join s-2) and their prefix sums.
+__device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v, unsigned long long* s_w,
+                                                                unsigned long long* total) {
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x / kWarp;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane >= o) x += y;
+    }
+    if ((int)lane == kWarp - 1) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long t = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if ((int)lane >= o) t += y;
+        }
+        s_w[lane] = t;
+    }
+    __syncthreads();
+    const unsigned long long r = (warp ? s_w[warp - 1] : 0ull) + x - v;
+    *total = s_w[kWarp - 1];
+    __syncthreads();
+    return r;
+}
+
 __global__ void __launch_bounds__(kSetupThreads)
     batch_setup_kernel(const eiger_join_desc* __restrict__ descs, int k, int chunk, float load,
                        unsigned long long max_slots, BatchMeta* __restrict__ meta,
-                       unsigned long long* __restrict__ item_prefix, unsigned* __restrict__ built,
-                       long long* __restrict__ counts, BatchCtrl* __restrict__ bc, int* status) {
-    __shared__ unsigned long long s_w[2][kSetupThreads / kWarp];
-    const unsigned lane = lane_id();
-    const int warp = threadIdx.x / kWarp;
-    unsigned long long slot_carry = 0, item_carry = 0;
+                       unsigned long long* __restrict__ stage_prefix, unsigned* __restrict__ built,
+                       unsigned* __restrict__ cleared, long long* __restrict__ counts, BatchCtrl* __restrict__ bc,
+                       int* status) {
+    __shared__ unsigned long long s_w[kSetupThreads / kWarp];
+    unsigned long long slot_carry = 0, item_carry = 0, total;
     for (int base = 0; base < k; base += kSetupThreads) {
         const int j = base + threadIdx.x;
-        unsigned long long slots = 0, items = 0, nbi = 0;
+        unsigned long long slots = 0;
         if (j < k) {
             const long long nb = descs[j].nb, np = descs[j].np;
+            BatchMeta m{};
             if (nb > 0 && np > 0) {
                 const double want = (double)nb / (double)load;
-                unsigned long long s = 64;
-                while ((double)s < want) s <<= 1;
-                slots = s;
-                nbi = (unsigned long long)((nb + chunk - 1) / chunk);
-                items = nbi + (unsigned long long)((np + chunk - 1) / chunk);
+                unsigned long long sl = 64;
+                while ((double)sl < want) sl <<= 1;
+                slots = sl;
+                m.slots = (uint32_t)sl;
+                m.nci = (uint32_t)((sl + kClearSlots - 1) / kClearSlots);
+                m.nbi = (uint32_t)((nb + chunk - 1) / chunk);
+                m.npi = (uint32_t)((np + chunk - 1) / chunk);
             }
+            meta[j] = m;
             built[j] = 0;
+            cleared[j] = 0;
             counts[j] = 0;
         }
-        // block exclusive scans of slots and items
-        unsigned long long xs = slots, xi = items;
-#pragma unroll
-        for (int o = 1; o < kWarp; o <<= 1) {
-            const unsigned long long ys = __shfl_up_sync(0xffffffffu, xs, o);
-            const unsigned long long yi = __shfl_up_sync(0xffffffffu, xi, o);
-            if ((int)lane >= o) {
-                xs += ys;
-                xi += yi;
-            }
+        const unsigned long long off = slot_carry + block_excl_scan64(slots, s_w, &total);
+        if (j < k) meta[j].table_off = off;
+        slot_carry += total;
+    }
+    __syncthreads();
+    __threadfence_block();
+    const int nstages = k + 2;
+    for (int base = 0; base < nstages; base += kSetupThreads) {
+        const int st = base + threadIdx.x;
+        unsigned long long items = 0;
+        if (st < nstages) {
+            if (st < k) items += meta[st].nci;
+            if (st >= 1 && st - 1 < k) items += meta[st - 1].nbi;
+            if (st >= 2) items += meta[st - 2].npi;
         }
-        if ((int)lane == kWarp - 1) {
-            s_w[0][warp] = xs;
-            s_w[1][warp] = xi;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            unsigned long long vs = s_w[0][lane], vi = s_w[1][lane];
-#pragma unroll
-            for (int o = 1; o < kWarp; o <<= 1) {
-                const unsigned long long ys = __shfl_up_sync(0xffffffffu, vs, o);
-                const unsigned long long yi = __shfl_up_sync(0xffffffffu, vi, o);
-                if ((int)lane >= o) {
-                    vs += ys;
-                    vi += yi;
-                }
-            }
-            s_w[0][lane] = vs;
-            s_w[1][lane] = vi;
-        }
-        __syncthreads();
-        const unsigned long long off_s = slot_carry + (warp ? s_w[0][warp - 1] : 0ull) + xs - slots;
-        const unsigned long long off_i = item_carry + (warp ? s_w[1][warp - 1] : 0ull) + xi - items;
-        if (j < k) {
-            meta[j].table_off = off_s;
-            meta[j].slots = (uint32_t)slots;
-            meta[j].nbi = (uint32_t)nbi;
-            item_prefix[j] = off_i;
-        }
-        slot_carry += s_w[0][kWarp - 1];
-        item_carry += s_w[1][kWarp - 1];
-        __syncthreads();
+        const unsigned long long off = item_carry + block_excl_scan64(items, s_w, &total);
+        if (st < nstages) stage_prefix[st] = off;
+        item_carry += total;
     }
     if (threadIdx.x == 0) {
-        item_prefix[k] = item_carry;
+        stage_prefix[nstages] = item_carry;
         bc->next_item = 0;
         bc->err = 0;
         bc->total_slots = slot_carry;
@@ -130,16 +148,7 @@ __global__ void __launch_bounds__(kSetupThreads)
     }
 }
 
-// Fills the table region with all-ones words (the empty slot of both layouts).
-__global__ void batch_clear_kernel(unsigned long long* __restrict__ words, const BatchCtrl* __restrict__ bc,
-                                   int words_per_slot) {
-    const unsigned long long n = bc->total_items ? bc->total_slots * (unsigned long long)words_per_slot : 0ull;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        words[i] = kEmptySlot;
-}
-
-// Warp-collective: the join j whose items contain `item` (last j with prefix[j] <= item).
+// Warp-collective: the stage whose items contain `item` (last s with prefix[s] <= item).
 __device__ __forceinline__ int find_join(const unsigned long long* __restrict__ prefix, int k,
                                          unsigned long long item) {
     const unsigned lane = lane_id();
@@ -159,15 +168,15 @@ __device__ __forceinline__ int find_join(const unsigned long long* __restrict__ 
 template <typename InKey, int THREADS>
 __global__ void __launch_bounds__(THREADS)
     batch_join_kernel(const eiger_join_desc* __restrict__ descs, int k, const BatchMeta* __restrict__ meta,
-                      const unsigned long long* __restrict__ item_prefix, unsigned char* __restrict__ tables,
-                      unsigned* __restrict__ built, long long* __restrict__ counts, BatchCtrl* bc, int chunk,
-                      int* status) {
+                      const unsigned long long* __restrict__ stage_prefix, unsigned char* __restrict__ tables,
+                      unsigned* __restrict__ built, unsigned* __restrict__ cleared, long long* __restrict__ counts,
+                      BatchCtrl* bc, int chunk, int* status) {
     constexpr bool kWide = sizeof(InKey) == 8;
     constexpr int kRows = 2;                   // probe rows per thread per round
     constexpr int kStage = THREADS * kRows * 2;
     __shared__ Stage<kStage> st;
     __shared__ unsigned long long s_item;
-    __shared__ int s_join;
+    __shared__ int s_stage;
     __shared__ int s_ready;
     const unsigned lane = lane_id();
     AggState agg{0ull, 0ull};
@@ -179,22 +188,67 @@ __global__ void __launch_bounds__(THREADS)
             unsigned long long it = 0;
             if (lane == 0) it = atomicAdd(&bc->next_item, 1ull);
             it = __shfl_sync(0xffffffffu, it, 0);
-            const int j = it < total ? find_join(item_prefix, k, it) : 0;
+            const int sg = it < total ? find_join(stage_prefix, k + 2, it) : 0;
             if (lane == 0) {
                 s_item = it;
-                s_join = j;
+                s_stage = sg;
             }
         }
         __syncthreads();
         const unsigned long long item = s_item;
-        const int j = s_join;
+        const int sg = s_stage;
         if (item >= total) break;
+        // decode: the clear items of join sg, then the build items of join
+        // sg - 1, then the probe items of join sg - 2
+        unsigned long long local = item - stage_prefix[sg];
+        int kind = 0, j = sg;
+        if (sg < k && local < meta[sg].nci) {
+            kind = 0;
+        } else {
+            if (sg < k) local -= meta[sg].nci;
+            j = sg - 1;
+            kind = 1;
+            if (!(j >= 0 && j < k && local < meta[j].nbi)) {
+                if (j >= 0 && j < k) local -= meta[j].nbi;
+                j = sg - 2;
+                kind = 2;
+            }
+        }
         const eiger_join_desc d = descs[j];
         const BatchMeta m = meta[j];
-        const unsigned long long local = item - item_prefix[j];
         const uint32_t mask = m.slots - 1;
 
-        if (local < m.nbi) {
+        if (kind == 0) {
+            // ---- clear chunk: kClearSlots slots of the join's table to the empty word
+            constexpr int kWords = kWide ? 2 : 1;
+            unsigned long long* w = reinterpret_cast<unsigned long long*>(tables) + m.table_off * kWords;
+            const unsigned long long lo = local * kClearSlots * kWords;
+            const unsigned long long hi0 = (local + 1) * kClearSlots * kWords;
+            const unsigned long long hi = hi0 < (unsigned long long)m.slots * kWords ? hi0 : (unsigned long long)m.slots * kWords;
+            for (unsigned long long i = lo + threadIdx.x; i < hi; i += THREADS) w[i] = kEmptySlot;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&cleared[j], 1u);
+            }
+        } else if (kind == 1) {
+            // ---- build chunk: wait until the join's table is cleared
+            if (threadIdx.x == 0) {
+                const volatile unsigned* cp = cleared + j;
+                int ok = 0;
+                for (uint32_t i = 0; i < kWaitLimit; ++i) {
+                    if (*cp >= m.nci) {
+                        ok = 1;
+                        break;
+                    }
+                    __nanosleep(i < 64 ? 32 : 256);
+                }
+                __threadfence();
+                if (!ok) atomicOr(&bc->err, kErrInternal);
+                s_ready = ok;
+            }
+            __syncthreads();
+            if (!s_ready) continue;
             // ---- build chunk
             const long long r0 = (long long)local * chunk;
             const long long r1 = r0 + chunk < d.nb ? r0 + chunk : d.nb;
@@ -253,7 +307,7 @@ __global__ void __launch_bounds__(THREADS)
             }
             __syncthreads();
             if (s_ready) {
-                const long long c = (long long)(local - m.nbi);
+                const long long c = (long long)local;
                 const long long r0 = c * chunk;
                 const long long r1 = r0 + chunk < d.np ? r0 + chunk : d.np;
                 const InKey* keys = static_cast<const InKey*>(d.probe_keys);
@@ -346,8 +400,8 @@ cudaError_t launch_batch(const eiger_join_desc* d_descs, int k, const BatchLayou
     const int grid = resident_grid(kern, THREADS, di);
     ProfScope ps("batch_join", 0.0, stream);
     kern<<<grid, THREADS, 0, stream>>>(d_descs, k, reinterpret_cast<const BatchMeta*>(L.meta), L.item_prefix,
-                                       L.tables, L.built, d_counts, reinterpret_cast<BatchCtrl*>(L.ctrl), chunk,
-                                       d_status);
+                                       L.tables, L.built, L.cleared, d_counts, reinterpret_cast<BatchCtrl*>(L.ctrl),
+                                       chunk, d_status);
     return cudaGetLastError();
 }
 
@@ -357,8 +411,9 @@ BatchLayout batch_layout(Carve& c, int k, unsigned long long total_slots, int sl
     BatchLayout L;
     L.ctrl = c.take<unsigned char>(sizeof(BatchCtrl));
     L.meta = c.take<unsigned char>(sizeof(BatchMeta) * (size_t)(k > 0 ? k : 1));
-    L.item_prefix = c.take<unsigned long long>((size_t)k + 1);
+    L.item_prefix = c.take<unsigned long long>((size_t)k + 3);  // stage prefix sums
     L.built = c.take<unsigned>((size_t)(k > 0 ? k : 1));
+    L.cleared = c.take<unsigned>((size_t)(k > 0 ? k : 1));
     L.tables = c.take<unsigned char>((size_t)total_slots * slot_bytes);
     L.table_slots = total_slots;
     return L;
@@ -375,14 +430,7 @@ cudaError_t batch_run(const eiger_join_desc* d_descs, int k, int dtype, const ei
         ProfScope ps("batch_setup", 0.0, stream);
         batch_setup_kernel<<<1, kSetupThreads, 0, stream>>>(d_descs, k, knobs.chunk_rows, knobs.load_factor,
                                                             L.table_slots, meta, L.item_prefix, L.built,
-                                                            d_counts, bc, d_status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const int wps = dtype == EIGER_I32 ? 1 : 2;
-    {
-        ProfScope ps("batch_clear", 8.0 * wps * (double)L.table_slots, stream);
-        batch_clear_kernel<<<di.sms * 4, 512, 0, stream>>>(reinterpret_cast<unsigned long long*>(L.tables), bc,
-                                                           wps);
+                                                            L.cleared, d_counts, bc, d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     switch (knobs.block_threads) {

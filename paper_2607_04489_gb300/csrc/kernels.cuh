@@ -228,8 +228,9 @@ eiger_plan_t class_plan(int cls);
 struct BatchLayout {
     unsigned char* ctrl;
     unsigned char* meta;
-    unsigned long long* item_prefix;  // [k + 1]
-    unsigned* built;                  // [k]
+    unsigned long long* item_prefix;  // [k + 3] item prefix of the k + 2 stages
+    unsigned* built;                  // [k] build rows inserted per join
+    unsigned* cleared;                // [k] clear items done per join
     unsigned char* tables;
     unsigned long long table_slots;   // capacity of `tables` in slots
 };
