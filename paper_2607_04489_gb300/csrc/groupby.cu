@@ -106,18 +106,27 @@ __device__ __forceinline__ uint64_t cas_key(uint64_t* p, uint64_t expect, uint64
 template <typename KeyT>
 struct GbTable {
     KeyT* keys;         // [slots + 1]; keys[slots] unused (the special slot is flagged below)
-    long long* aggs;    // [naggs][slots + 1]
+    long long* aggs;    // [naggs][stride]
     unsigned* special;  // 1 when the all-ones key has been seen
     unsigned long long slots;
+    unsigned long long stride;                // >= slots + 1
+    const unsigned long long* slots_dev;      // when set, kernels read the slot count here
 };
+
+// Kernels that get a table whose size was decided on the device read it first.
+template <typename KeyT>
+__device__ __forceinline__ void resolve_slots(GbTable<KeyT>& t) {
+    if (t.slots_dev) t.slots = *t.slots_dev;
+}
 
 template <typename KeyT>
 __global__ void gb_init_kernel(GbTable<KeyT> t, AggSpec s) {
+    resolve_slots(t);
     const unsigned long long total = t.slots + 1;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         t.keys[i] = Empty<KeyT>::v;
-        for (int a = 0; a < s.n; ++a) t.aggs[(size_t)a * total + i] = agg_init(s.op[a]);
+        for (int a = 0; a < s.n; ++a) t.aggs[(size_t)a * t.stride + i] = agg_init(s.op[a]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *t.special = 0;
 }
@@ -149,7 +158,7 @@ template <typename InKey, typename KeyT>
 __global__ void __launch_bounds__(kGbThreads)
     gb_hash_global_kernel(const InKey* __restrict__ keys, uint32_t n, uint64_t offset, GbTable<KeyT> t, AggSpec s,
                           unsigned* err) {
-    const unsigned long long total = t.slots + 1;
+    const unsigned long long total = t.stride;
     for (unsigned long long rr = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; rr < n;
          rr += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t r = (uint32_t)rr;
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(kGbThreads)
                 const unsigned long long g = gb_global_slot(t, k, err);
                 if (g != ~0ull)
                     for (int a = 0; a < s.n; ++a)
-                        agg_atomic(s.op[a], t.aggs + (size_t)a * (t.slots + 1) + g, agg_value(s, a, r));
+                        agg_atomic(s.op[a], t.aggs + (size_t)a * t.stride + g, agg_value(s, a, r));
                 ok = false;
             }
         }
@@ -272,7 +281,7 @@ __global__ void __launch_bounds__(kGbThreads)
     (void)full;
     __syncthreads();
     // merge the CTA's groups into the global table
-    const unsigned long long total = t.slots + 1;
+    const unsigned long long total = t.stride;
     for (uint32_t i = threadIdx.x; i <= tab.tsize; i += blockDim.x) {
         unsigned long long g;
         if (i == tab.tsize) {
@@ -310,6 +319,7 @@ __device__ __forceinline__ void write_group(const GbOut& o, unsigned long long p
 // Occupied slots of the global table -> output, reserved per warp.
 template <typename KeyT>
 __global__ void gb_compact_kernel(GbTable<KeyT> t, AggSpec s, uint64_t offset, GbOut o, Ctrl* ctrl) {
+    resolve_slots(t);
     const unsigned long long total = t.slots + 1;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long start = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
@@ -330,7 +340,7 @@ __global__ void gb_compact_kernel(GbTable<KeyT> t, AggSpec s, uint64_t offset, G
         if (has) {
             const KeyT k = i == t.slots ? Empty<KeyT>::v : t.keys[i];
             long long v[kMaxCols];
-            for (int a = 0; a < s.n; ++a) v[a] = t.aggs[(size_t)a * total + i];
+            for (int a = 0; a < s.n; ++a) v[a] = t.aggs[(size_t)a * t.stride + i];
             write_group(o, base + __popc(m & lanemask_lt()), (int64_t)((uint64_t)k + offset), v, s.n);
         }
     }
@@ -338,38 +348,140 @@ __global__ void gb_compact_kernel(GbTable<KeyT> t, AggSpec s, uint64_t offset, G
 
 // ------------------------------------------------------------------ partition variant
 
-template <typename KeyT>
-struct GbPartIn {
-    const KeyT* key;          // partitioned keys
-    const uint32_t* start;    // [P + 1]
-    uint32_t P;
-    AggSpec s;                // value columns: the partitioned copies
-};
+constexpr uint32_t kGbChunk = 65536;  // rows per work item of the partition variant
 
 template <typename KeyT>
+struct GbPartIn {
+    const KeyT* key;                          // partitioned keys
+    const uint32_t* start;                    // [P + 1]
+    const unsigned long long* item_prefix;    // [P + 1] work items before each partition
+    uint32_t P;
+    AggSpec s;                                // value columns: the partitioned copies
+};
+
+// One block: work items per partition (row chunks of kGbChunk), their
+// exclusive prefix, the item total (ctrl->nitems) and the slots of the spill
+// table for the groups of partitions that span several items: at most
+// kPartSlots groups each, at load <= 1/2, capped at spill_max.
+__global__ void __launch_bounds__(1024)
+    gb_items_kernel(const uint32_t* __restrict__ start, uint32_t P, unsigned long long* __restrict__ prefix,
+                    Ctrl* ctrl, unsigned long long* spill_slots, unsigned long long spill_max) {
+    __shared__ unsigned long long s_w[1024 / kWarp];
+    __shared__ unsigned long long s_m[1024 / kWarp];
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x / kWarp;
+    unsigned long long carry = 0, multi = 0;
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t p = base + threadIdx.x;
+        unsigned long long items = 0;
+        if (p < P) {
+            const uint32_t rows = start[p + 1] - start[p];
+            items = (rows + kGbChunk - 1) / kGbChunk;
+        }
+        unsigned long long x = items, m = items > 1;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            const unsigned long long z = __shfl_up_sync(0xffffffffu, m, o);
+            if ((int)lane >= o) {
+                x += y;
+                m += z;
+            }
+        }
+        if ((int)lane == kWarp - 1) {
+            s_w[w] = x;
+            s_m[w] = m;
+        }
+        __syncthreads();
+        if (w == 0) {
+            unsigned long long t = s_w[lane], u = s_m[lane];
+#pragma unroll
+            for (int o = 1; o < kWarp; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+                const unsigned long long z = __shfl_up_sync(0xffffffffu, u, o);
+                if ((int)lane >= o) {
+                    t += y;
+                    u += z;
+                }
+            }
+            s_w[lane] = t;
+            s_m[lane] = u;
+        }
+        __syncthreads();
+        if (p < P) prefix[p] = carry + (w ? s_w[w - 1] : 0ull) + x - items;
+        carry += s_w[kWarp - 1];
+        multi += s_m[kWarp - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        prefix[P] = carry;
+        ctrl->nitems = carry;
+        unsigned long long sl = 64;
+        while (sl < 2ull * kPartSlots * multi && sl < spill_max) sl <<= 1;
+        *spill_slots = multi ? (sl < spill_max ? sl : spill_max) : 0ull;
+    }
+}
+
+// Warp-collective: the partition of work item `item` (last p with prefix[p] <= item).
+__device__ __forceinline__ uint32_t find_item_part(const unsigned long long* __restrict__ prefix, uint32_t P,
+                                                   unsigned long long item) {
+    const unsigned lane = lane_id();
+    uint32_t lo = 0, hi = P;
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + kWarp - 1) / kWarp;
+        const uint32_t piv = lo + lane * step;
+        const bool le = piv < hi && prefix[piv] <= item;
+        const unsigned m = __ballot_sync(0xffffffffu, le);
+        lo = lo + (31 - __clz(m)) * step;
+        hi = lo + step < hi ? lo + step : hi;
+    }
+    return lo;
+}
+
+// A persistent grid takes work items (a partition's chunk of kGbChunk rows)
+// from a global counter and aggregates each in a shared-memory table. A
+// partition that is one item writes its groups out directly; the items of a
+// larger partition (few groups, many rows) merge their groups into the spill
+// table, which is compacted afterwards.
+template <typename KeyT>
 __global__ void __launch_bounds__(kGbThreads)
-    gb_part_kernel(GbPartIn<KeyT> a, uint64_t offset, GbOut o, Ctrl* ctrl) {
+    gb_part_kernel(GbPartIn<KeyT> a, GbTable<KeyT> spill, uint64_t offset, GbOut o, Ctrl* ctrl) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_scratch[kGbThreads];
     __shared__ uint32_t s_warp[kGbThreads / kWarp];
     __shared__ unsigned s_special;
     __shared__ unsigned long long s_item;
+    __shared__ uint32_t s_part;
     __shared__ unsigned long long s_base;
     __shared__ int s_full;
+    resolve_slots(spill);
     SmemGb<KeyT> tab;
     tab.bind(smem, kPartSlots);
     long long* scratch = s_scratch + (threadIdx.x & ~(kWarp - 1));
+    const unsigned long long nitems = ctrl->nitems;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl->next_item, 1ull);
-        tab.clear(a.s);
-        if (threadIdx.x == 0) {
-            s_special = 0;
-            s_full = 0;
+        if (threadIdx.x < kWarp) {
+            unsigned long long it = 0;
+            if (threadIdx.x == 0) it = atomicAdd(&ctrl->next_item, 1ull);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            const uint32_t p = it < nitems ? find_item_part(a.item_prefix, a.P, it) : 0u;
+            if (threadIdx.x == 0) {
+                s_item = it;
+                s_part = p;
+                s_special = 0;
+                s_full = 0;
+            }
         }
+        tab.clear(a.s);
         __syncthreads();
-        const unsigned long long p = s_item;
-        if (p >= a.P) break;
-        const uint32_t beg = a.start[p], end = a.start[p + 1];
+        const unsigned long long item = s_item;
+        if (item >= nitems) break;
+        const uint32_t p = s_part;
+        const unsigned long long c = item - a.item_prefix[p];
+        const bool multi = a.item_prefix[p + 1] - a.item_prefix[p] > 1;
+        const uint32_t pend = a.start[p + 1];
+        const unsigned long long beg = (unsigned long long)a.start[p] + c * kGbChunk;
+        const unsigned long long end = beg + kGbChunk < pend ? beg + kGbChunk : pend;
         for (unsigned long long base = beg; base < end; base += kGbThreads) {
             const uint32_t r = (uint32_t)(base + threadIdx.x);
             bool ok = base + threadIdx.x < end;
@@ -387,6 +499,25 @@ __global__ void __launch_bounds__(kGbThreads)
         __syncthreads();
         if (s_full) {  // more groups than one table: the host repartitions with more bits
             if (threadIdx.x == 0) atomicOr(&ctrl->err, kErrTableFull);
+            __syncthreads();
+            continue;
+        }
+        if (multi) {
+            // merge this item's groups into the spill table
+            for (uint32_t i = threadIdx.x; i <= kPartSlots; i += blockDim.x) {
+                KeyT k;
+                if (i == kPartSlots) {
+                    if (!s_special) continue;
+                    k = Empty<KeyT>::v;
+                } else {
+                    k = tab.keys[i];
+                    if (k == Empty<KeyT>::v) continue;
+                }
+                const unsigned long long g = gb_global_slot(spill, k, &ctrl->err);
+                if (g == ~0ull) continue;
+                for (int b = 0; b < a.s.n; ++b)
+                    agg_atomic(a.s.op[b], spill.aggs + (size_t)b * spill.stride + g, *tab.agg(b, i));
+            }
             __syncthreads();
             continue;
         }
@@ -454,6 +585,8 @@ cudaError_t gb_hash_run(const GbArgs& g, const GbPlanDev& plan, const GbScratch&
     t.aggs = c.take<long long>((size_t)s.n * (plan.slots + 1));
     t.special = c.take<unsigned>(1);
     t.slots = plan.slots;
+    t.stride = plan.slots + 1;
+    t.slots_dev = nullptr;
     cudaError_t e;
     const double kb = (double)sizeof(KeyT);
     {
@@ -522,10 +655,29 @@ cudaError_t gb_part_run(const GbArgs& g, const GbPlanDev& plan, const GbScratch&
     cudaError_t e = partition_side(g.keys, g.n, 0, pd, sc.part, &carry, &ctrl->err, stream);
     if (e != cudaSuccess) return e;
     const int buf = plan.bits2 ? 1 : 0;
+    const uint32_t P = 1u << (plan.bits1 + plan.bits2);
+    GbTable<KeyT> spill;
+    {
+        Carve c{static_cast<char*>(sc.spill), 0};
+        spill.keys = c.take<KeyT>(sc.spill_max + 1);
+        spill.aggs = c.take<long long>((size_t)s.n * (sc.spill_max + 1));
+        spill.special = c.take<unsigned>(1);
+        spill.slots = sc.spill_max;
+        spill.stride = sc.spill_max + 1;
+        spill.slots_dev = sc.spill_slots;
+    }
+    {
+        ProfScope ps("gb_items", 8.0 * P, stream, 0.0, 2);
+        gb_items_kernel<<<1, 1024, 0, stream>>>(sc.part.part_start, P, sc.item_prefix, ctrl, sc.spill_slots,
+                                                sc.spill_max);
+        gb_init_kernel<KeyT><<<di.sms * 2, 256, 0, stream>>>(spill, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     GbPartIn<KeyT> in;
     in.key = static_cast<const KeyT*>(sc.part.key[buf]);
     in.start = sc.part.part_start;
-    in.P = 1u << (plan.bits1 + plan.bits2);
+    in.item_prefix = sc.item_prefix;
+    in.P = P;
     in.s = s;
     for (int a = 0; a < s.n; ++a)
         if (col_of[a] >= 0) in.s.vals[a] = sc.part.col[buf][col_of[a]];
@@ -538,8 +690,15 @@ cudaError_t gb_part_run(const GbArgs& g, const GbPlanDev& plan, const GbScratch&
         per_sm = 1;
     double vbytes = 0;
     for (int a = 0; a < s.n; ++a) vbytes += s.op[a] == EIGER_AGG_COUNT ? 0 : s.bytes[a];
-    ProfScope ps("gb_part", ((double)sizeof(KeyT) + vbytes) * (double)g.n, stream, (double)sizeof(InKey) + 8.0 * s.n);
-    kern<<<di.sms * per_sm, kGbThreads, smem, stream>>>(in, plan.offset, o, ctrl);
+    {
+        ProfScope ps("gb_part", ((double)sizeof(KeyT) + vbytes) * (double)g.n, stream,
+                     (double)sizeof(InKey) + 8.0 * s.n);
+        kern<<<di.sms * per_sm, kGbThreads, smem, stream>>>(in, spill, plan.offset, o, ctrl);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // the groups of multi-item partitions (an empty spill table when there are none)
+    ProfScope ps("gb_spill_compact", 0.0, stream);
+    gb_compact_kernel<KeyT><<<di.sms * 2, 256, 0, stream>>>(spill, s, plan.offset, o, ctrl);
     return cudaGetLastError();
 }
 
@@ -563,6 +722,18 @@ GbScratch gb_layout(Carve& c, int64_t n, const GbPlanDev& plan, const int* col_b
         for (int q = 0; q < ncols; ++q) pd.col_bytes[0][q] = col_bytes[q];
         const int passes = plan.bits2 ? 2 : 1;
         part_side_layout(c, s.part, n, plan.bits1, plan.bits2, passes, false, plan.key32 ? 4 : 8, pd, 0);
+        // spill table: each multi-item partition has more than kGbChunk rows and at
+        // most kPartSlots groups; load <= 1/2
+        const unsigned long long nn = n > 0 ? (unsigned long long)n : 1ull;
+        unsigned long long groups = (nn / kGbChunk + 1) * kPartSlots;
+        if (groups > nn) groups = nn;
+        unsigned long long sl = 64;
+        while (sl < 2 * groups) sl <<= 1;
+        s.spill_max = sl;
+        s.spill = c.take<unsigned char>(plan.key32 ? gb_global_bytes<uint32_t>(sl, plan.naggs)
+                                                   : gb_global_bytes<uint64_t>(sl, plan.naggs));
+        s.spill_slots = c.take<unsigned long long>(1);
+        s.item_prefix = c.take<unsigned long long>(((size_t)1 << (plan.bits1 + plan.bits2)) + 1);
     }
     return s;
 }

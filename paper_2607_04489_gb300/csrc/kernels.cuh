@@ -200,6 +200,10 @@ struct GbAggs {
 struct GbScratch {
     void* table;   // hash: keys, aggregates, special flag
     PartSide part; // partition: the partitioned keys and carried value columns
+    void* spill;                       // partition: table of the groups of multi-item partitions
+    unsigned long long spill_max;      // its capacity in slots
+    unsigned long long* spill_slots;   // its size, decided on the device
+    unsigned long long* item_prefix;   // [P + 1] work items per partition, prefix
 };
 
 // Shared-memory bytes of a CTA-private table of `slots` slots.
