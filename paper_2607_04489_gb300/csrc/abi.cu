@@ -43,6 +43,42 @@ cudaError_t current_device_info(DevInfo* out) {
     return cudaSuccess;
 }
 
+namespace {
+
+struct SideStreams {
+    cudaStream_t side[64] = {};
+    cudaEvent_t fork[64] = {};
+    cudaEvent_t join[64] = {};
+};
+thread_local SideStreams g_side;
+
+}  // namespace
+
+cudaError_t fork_side(cudaStream_t main, cudaStream_t* side) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!g_side.side[dev]) {
+        if ((e = cudaStreamCreateWithFlags(&g_side.side[dev], cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&g_side.fork[dev], cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&g_side.join[dev], cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventRecord(g_side.fork[dev], main)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(g_side.side[dev], g_side.fork[dev], 0)) != cudaSuccess) return e;
+    *side = g_side.side[dev];
+    return cudaSuccess;
+}
+
+cudaError_t join_side(cudaStream_t main, cudaStream_t side) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || side != g_side.side[dev]) return cudaErrorInvalidValue;
+    if ((e = cudaEventRecord(g_side.join[dev], side)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(main, g_side.join[dev], 0);
+}
+
 }  // namespace eiger
 
 using namespace eiger;

@@ -26,6 +26,16 @@ void prof_set_matches(unsigned long long m);
 bool prof_set_enabled(bool on);  // returns the previous setting
 double match_bytes(const JoinOut& out);
 
+// ------------------------------------------------------------------ streams
+
+// A second stream of the calling host thread on the current device, for work
+// of a call that can run beside the main stream (the build and probe sides'
+// partitioning). fork_side makes it wait for everything enqueued on `main`;
+// join_side makes `main` wait for everything enqueued on it. Created once per
+// host thread and device; no device memory is allocated.
+cudaError_t fork_side(cudaStream_t main, cudaStream_t* side);
+cudaError_t join_side(cudaStream_t main, cudaStream_t side);
+
 // ------------------------------------------------------------------ stats
 
 constexpr int kStatsMaxGrid = 512;

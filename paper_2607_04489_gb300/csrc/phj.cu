@@ -542,10 +542,14 @@ cudaError_t phj_run(const JoinArgs& a, const PlanDev& plan, const PhjScratch& s,
     DevInfo di;
     cudaError_t e = current_device_info(&di);
     if (e != cudaSuccess) return e;
-    if ((e = partition_side(a.bkeys, a.nb, 0, plan, s.side[0], &out.b, &ctrl->err, stream)) != cudaSuccess)
+    // the two sides are partitioned concurrently: build on a second stream
+    cudaStream_t side;
+    if ((e = fork_side(stream, &side)) != cudaSuccess) return e;
+    if ((e = partition_side(a.bkeys, a.nb, 0, plan, s.side[0], &out.b, &ctrl->err, side)) != cudaSuccess)
         return e;
     if ((e = partition_side(a.pkeys, a.np, 1, plan, s.side[1], &out.p, &ctrl->err, stream)) != cudaSuccess)
         return e;
+    if ((e = join_side(stream, side)) != cudaSuccess) return e;
     const int passes = plan.variant == 3 ? 2 : 1;
     // GFTR: gather from the partitioned copies at the positions the join emits
     const JoinOut o = plan.gftr ? gftr_out(out, s.side[0], s.side[1], passes - 1) : out;

@@ -267,8 +267,12 @@ cudaError_t smj_run(const JoinArgs& a, const PlanDev& plan, const SmjScratch& s,
     DevInfo di;
     cudaError_t e = current_device_info(&di);
     if (e != cudaSuccess) return e;
-    if ((e = sort_side(a.bkeys, a.nb, 0, plan, s.side[0], &out.b, &ctrl->err, stream)) != cudaSuccess) return e;
+    // the two sides are sorted concurrently: build on a second stream
+    cudaStream_t side;
+    if ((e = fork_side(stream, &side)) != cudaSuccess) return e;
+    if ((e = sort_side(a.bkeys, a.nb, 0, plan, s.side[0], &out.b, &ctrl->err, side)) != cudaSuccess) return e;
     if ((e = sort_side(a.pkeys, a.np, 1, plan, s.side[1], &out.p, &ctrl->err, stream)) != cudaSuccess) return e;
+    if ((e = join_side(stream, side)) != cudaSuccess) return e;
     const JoinOut o = plan.gftr ? gftr_out(out, s.side[0], s.side[1], (plan.bits2 - 1) & 1) : out;
     return plan.key32 ? launch_smj<uint32_t>(s, plan, o, ctrl, di, stream, a.nb, a.np)
                       : launch_smj<uint64_t>(s, plan, o, ctrl, di, stream, a.nb, a.np);
