@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(kSetupThreads)
     batch_setup_kernel(const eiger_join_desc* __restrict__ descs, int k, int chunk, float load,
                        unsigned long long max_slots, BatchMeta* __restrict__ meta,
                        unsigned long long* __restrict__ stage_prefix, unsigned* __restrict__ built,
-                       unsigned* __restrict__ cleared, long long* __restrict__ counts, BatchCtrl* __restrict__ bc,
-                       int* status) {
+                       unsigned* __restrict__ cleared, unsigned* __restrict__ dup, long long* __restrict__ counts,
+                       BatchCtrl* __restrict__ bc, int* status) {
     __shared__ unsigned long long s_w[kSetupThreads / kWarp];
     unsigned long long slot_carry = 0, item_carry = 0, total;
     for (int base = 0; base < k; base += kSetupThreads) {
@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(kSetupThreads)
             meta[j] = m;
             built[j] = 0;
             cleared[j] = 0;
+            dup[j] = 0;
             counts[j] = 0;
         }
         const unsigned long long off = slot_carry + block_excl_scan64(slots, s_w, &total);
@@ -169,8 +170,8 @@ template <typename InKey, int THREADS>
 __global__ void __launch_bounds__(THREADS)
     batch_join_kernel(const eiger_join_desc* __restrict__ descs, int k, const BatchMeta* __restrict__ meta,
                       const unsigned long long* __restrict__ stage_prefix, unsigned char* __restrict__ tables,
-                      unsigned* __restrict__ built, unsigned* __restrict__ cleared, long long* __restrict__ counts,
-                      BatchCtrl* bc, int chunk, int* status) {
+                      unsigned* __restrict__ built, unsigned* __restrict__ cleared, unsigned* __restrict__ dup,
+                      long long* __restrict__ counts, BatchCtrl* bc, int chunk, int* status) {
     constexpr bool kWide = sizeof(InKey) == 8;
     constexpr int kRows = 2;                   // probe rows per thread per round
     constexpr int kStage = THREADS * kRows * 2;
@@ -253,8 +254,11 @@ __global__ void __launch_bounds__(THREADS)
             const long long r0 = (long long)local * chunk;
             const long long r1 = r0 + chunk < d.nb ? r0 + chunk : d.nb;
             const InKey* keys = static_cast<const InKey*>(d.build_keys);
+            // the next row's key is loaded before this row's inserts
+            InKey knext = r0 + threadIdx.x < r1 ? __ldcs(keys + r0 + threadIdx.x) : InKey(0);
             for (long long r = r0 + threadIdx.x; r < r1; r += THREADS) {
-                const InKey key = keys[r];
+                const InKey key = knext;
+                if (r + THREADS < r1) knext = __ldcs(keys + r + THREADS);
                 if constexpr (kWide) {
                     WideSlot* t = reinterpret_cast<WideSlot*>(tables) + m.table_off;
                     uint32_t s = (uint32_t)mix64((uint64_t)key) & mask;
@@ -273,9 +277,11 @@ __global__ void __launch_bounds__(THREADS)
                     unsigned long long* t = reinterpret_cast<unsigned long long*>(tables) + m.table_off;
                     const uint32_t k32 = (uint32_t)key;
                     const unsigned long long v = ((unsigned long long)k32 << 32) | (uint32_t)r;
-                    uint32_t s = mix32(k32) & mask;
+                    uint32_t s = mix32(k32) & mask & ~1u;  // chains start at even slots (pair loads)
                     for (uint32_t step = 0;; ++step) {
-                        if (atomicCAS(t + s, kEmptySlot, v) == kEmptySlot) break;
+                        const unsigned long long prev = atomicCAS(t + s, kEmptySlot, v);
+                        if (prev == kEmptySlot) break;
+                        if ((uint32_t)(prev >> 32) == k32) dup[j] = 1u;  // an equal key lies on the path
                         if (step == mask) {
                             atomicOr(&bc->err, kErrTableFull);
                             break;
@@ -317,16 +323,54 @@ __global__ void __launch_bounds__(THREADS)
                 out.capacity = d.capacity > 0 ? (unsigned long long)d.capacity : 0ull;
                 unsigned long long* cursor = reinterpret_cast<unsigned long long*>(counts + j);
                 const long long round = (long long)THREADS * kRows;
+                // a join without duplicate build keys: each lane stops at its first match
+                const bool first = !kWide && __ldcg(dup + j) == 0u;
+                // each row's key is loaded one row ahead of its chain walk
+                long long rn = r0 + threadIdx.x;
+                InKey knext = rn < r1 ? __ldcs(keys + rn) : InKey(0);
                 for (long long base = r0; base < r1; base += round) {
 #pragma unroll 1
                     for (int it = 0; it < kRows; ++it) {
                         const long long r = base + (long long)it * THREADS + threadIdx.x;
+                        const InKey kraw = knext;
+                        rn = r + THREADS;
+                        if (rn < r1) knext = __ldcs(keys + rn);
                         bool active = r < r1;
                         InKey key = 0;
                         uint32_t s = 0, steps = 0;
                         if (active) {
-                            key = __ldcs(keys + r);
-                            s = kWide ? (uint32_t)mix64((uint64_t)key) & mask : mix32((uint32_t)key) & mask;
+                            key = kraw;
+                            s = kWide ? (uint32_t)mix64((uint64_t)key) & mask : mix32((uint32_t)key) & mask & ~1u;
+                        }
+                        if (first) {
+                            const unsigned long long* t =
+                                reinterpret_cast<const unsigned long long*>(tables) + m.table_off;
+                            bool hit = false;
+                            uint32_t bi = 0;
+                            if (active) {
+                                for (uint32_t step = 0;; step += 2) {
+                                    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(t + s));
+                                    if (v.x == kEmptySlot) break;
+                                    if ((uint32_t)(v.x >> 32) == (uint32_t)key) {
+                                        hit = true;
+                                        bi = (uint32_t)v.x;
+                                        break;
+                                    }
+                                    if (v.y == kEmptySlot) break;
+                                    if ((uint32_t)(v.y >> 32) == (uint32_t)key) {
+                                        hit = true;
+                                        bi = (uint32_t)v.y;
+                                        break;
+                                    }
+                                    if (step + 2 > mask) {
+                                        atomicOr(&bc->err, kErrTableFull);
+                                        break;
+                                    }
+                                    s = (s + 2) & mask;
+                                }
+                            }
+                            emit<false, kStage>(st, agg, hit, bi, (uint32_t)r, out, cursor);
+                            continue;
                         }
                         while (__any_sync(0xffffffffu, active)) {
                             bool hit = false;
@@ -400,7 +444,7 @@ cudaError_t launch_batch(const eiger_join_desc* d_descs, int k, const BatchLayou
     const int grid = resident_grid(kern, THREADS, di);
     ProfScope ps("batch_join", 0.0, stream);
     kern<<<grid, THREADS, 0, stream>>>(d_descs, k, reinterpret_cast<const BatchMeta*>(L.meta), L.item_prefix,
-                                       L.tables, L.built, L.cleared, d_counts, reinterpret_cast<BatchCtrl*>(L.ctrl),
+                                       L.tables, L.built, L.cleared, L.dup, d_counts, reinterpret_cast<BatchCtrl*>(L.ctrl),
                                        chunk, d_status);
     return cudaGetLastError();
 }
@@ -414,6 +458,7 @@ BatchLayout batch_layout(Carve& c, int k, unsigned long long total_slots, int sl
     L.item_prefix = c.take<unsigned long long>((size_t)k + 3);  // stage prefix sums
     L.built = c.take<unsigned>((size_t)(k > 0 ? k : 1));
     L.cleared = c.take<unsigned>((size_t)(k > 0 ? k : 1));
+    L.dup = c.take<unsigned>((size_t)(k > 0 ? k : 1));
     L.tables = c.take<unsigned char>((size_t)total_slots * slot_bytes);
     L.table_slots = total_slots;
     return L;
@@ -430,7 +475,7 @@ cudaError_t batch_run(const eiger_join_desc* d_descs, int k, int dtype, const ei
         ProfScope ps("batch_setup", 0.0, stream);
         batch_setup_kernel<<<1, kSetupThreads, 0, stream>>>(d_descs, k, knobs.chunk_rows, knobs.load_factor,
                                                             L.table_slots, meta, L.item_prefix, L.built,
-                                                            L.cleared, d_counts, bc, d_status);
+                                                            L.cleared, L.dup, d_counts, bc, d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     switch (knobs.block_threads) {

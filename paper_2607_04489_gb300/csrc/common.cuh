@@ -106,7 +106,8 @@ struct Ctrl {
     unsigned int err;              // kErr* flags
     unsigned int ntiles2[2];       // pass-2 tile count per side (build, probe)
     unsigned int kept[2];          // rows kept by the range test per side
-    unsigned int pad[3];
+    unsigned int dup;              // non-partitioned build: a key was inserted twice
+    unsigned int pad[2];
 };
 
 // Payload columns per side a wide join can materialise.
@@ -153,6 +154,28 @@ __device__ __forceinline__ void write_pay(void* p, int bytes, unsigned long long
         ((int32_t*)p)[i] = (int32_t)v;
     else
         ((int64_t*)p)[i] = v;
+}
+
+// ---------------------------------------------------------------- cache policies
+
+// An L2 policy that keeps lines resident ahead of normally cached ones: for
+// hash tables probed while other data streams through the cache.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ unsigned long long ld_keep(const unsigned long long* a, uint64_t pol) {
+    unsigned long long v;
+    asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ ulonglong2 ld_keep2(const ulonglong2* a, uint64_t pol) {
+    ulonglong2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;" : "=l"(v.x), "=l"(v.y) : "l"(a), "l"(pol));
+    return v;
 }
 
 // ---------------------------------------------------------------- TMA bulk copies

@@ -41,8 +41,9 @@ __device__ __forceinline__ void copy_cols(const ColSide& cs, unsigned long long 
 __device__ __forceinline__ void write_match(const JoinOut& out, unsigned long long pos, uint32_t b,
                                             uint32_t p) {
     if (pos >= out.capacity) return;
-    if (out.bidx) out.bidx[pos] = out.b.rowmap ? __ldg(out.b.rowmap + b) : b;
-    if (out.pidx) out.pidx[pos] = out.p.rowmap ? __ldg(out.p.rowmap + p) : p;
+    // outputs are written once and not read back here: streaming stores
+    if (out.bidx) __stcs(out.bidx + pos, out.b.rowmap ? __ldg(out.b.rowmap + b) : b);
+    if (out.pidx) __stcs(out.pidx + pos, out.p.rowmap ? __ldg(out.p.rowmap + p) : p);
     copy_cols(out.b, pos, b);
     copy_cols(out.p, pos, p);
 }

@@ -245,6 +245,7 @@ struct BatchLayout {
     unsigned long long* item_prefix;  // [k + 3] item prefix of the k + 2 stages
     unsigned* built;                  // [k] build rows inserted per join
     unsigned* cleared;                // [k] clear items done per join
+    unsigned* dup;                    // [k] 1 when a join's build keys repeat
     unsigned char* tables;
     unsigned long long table_slots;   // capacity of `tables` in slots
 };

@@ -11,6 +11,13 @@
 // Linear probing from mix(key') & (slots - 1). The static baseline is the same
 // machinery without statistics: raw keys, wide slots for int64, no probe range
 // test, load factor 0.5.
+//
+// Packed tables start every chain at an even slot, so a probe reads its slots
+// two at a time with one 16-byte load. The build records whether any key was
+// inserted twice: with packed slots an equal key always lies on the later
+// insert's path and is seen by its failed CAS. Without duplicates every probe
+// key has at most one match, so (outside the static baseline) each lane walks
+// its chain alone, stops at its first match and emits once.
 #include "emit.cuh"
 #include "kernels.cuh"
 
@@ -33,12 +40,19 @@ __global__ void __launch_bounds__(kBuildThreads)
     nphj_build_packed(const InKey* __restrict__ keys, int64_t n, uint64_t offset,
                       unsigned long long* __restrict__ table, uint32_t mask, Ctrl* ctrl) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-        const uint32_t k = KeyCodec<uint32_t>::encode((int64_t)keys[r], offset);
+    // the next row's key is loaded before this row's inserts (off the critical path)
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    InKey knext = r < n ? __ldcs(keys + r) : InKey(0);
+    for (; r < n; r += stride) {
+        const InKey kraw = knext;
+        if (r + stride < n) knext = __ldcs(keys + r + stride);
+        const uint32_t k = KeyCodec<uint32_t>::encode((int64_t)kraw, offset);
         const unsigned long long v = ((unsigned long long)k << 32) | (uint32_t)r;
-        uint32_t slot = mix32(k) & mask;
+        uint32_t slot = mix32(k) & mask & ~1u;
         for (uint32_t step = 0;; ++step) {
-            if (atomicCAS(table + slot, kEmptySlot, v) == kEmptySlot) break;
+            const unsigned long long prev = atomicCAS(table + slot, kEmptySlot, v);
+            if (prev == kEmptySlot) break;
+            if ((uint32_t)(prev >> 32) == k) ctrl->dup = 1u;
             if (step == mask) {
                 atomicOr(&ctrl->err, kErrTableFull);
                 break;
@@ -52,8 +66,11 @@ __global__ void __launch_bounds__(kBuildThreads)
     nphj_build_wide(const int64_t* __restrict__ keys, int64_t n, WideSlot* __restrict__ table,
                     unsigned long long mask, Ctrl* ctrl) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-        const uint64_t k = (uint64_t)keys[r];
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t knext = r < n ? __ldcs(keys + r) : 0;
+    for (; r < n; r += stride) {
+        const uint64_t k = (uint64_t)knext;
+        if (r + stride < n) knext = __ldcs(keys + r + stride);
         unsigned long long slot = mix64(k) & mask;
         for (unsigned long long step = 0;; ++step) {
             if (atomicCAS(&table[slot].row, kEmptySlot, (unsigned long long)r) == kEmptySlot) {
@@ -73,29 +90,67 @@ template <typename InKey, bool AGG>
 __global__ void __launch_bounds__(kProbeThreads)
     nphj_probe_packed(const InKey* __restrict__ keys, int64_t n, KeyRange rng, int check_range,
                       const unsigned long long* __restrict__ table, uint32_t mask, JoinOut out,
-                      Ctrl* ctrl) {
+                      Ctrl* ctrl, int allow_first_match) {
     __shared__ Stage<kStage> st;
     if (threadIdx.x == 0) st.count = 0;
     __syncthreads();
     AggState agg{0ull, 0ull};
+    const uint64_t keep = l2_keep_policy();  // the table stays in L2 while keys and pairs stream
+    const bool first_match = allow_first_match && ctrl->dup == 0u;
     const int64_t round = (int64_t)kProbeThreads * kProbeItems;
-    for (int64_t base = (int64_t)blockIdx.x * round; base < n; base += (int64_t)gridDim.x * round) {
+    const int64_t grid_round = (int64_t)gridDim.x * round;
+    // each row's key is loaded one row ahead, so a chain walk waits only on its slots
+    int64_t rn = (int64_t)blockIdx.x * round + threadIdx.x;
+    InKey knext = rn < n ? __ldcs(keys + rn) : InKey(0);
+    for (int64_t base = (int64_t)blockIdx.x * round; base < n; base += grid_round) {
 #pragma unroll 1
         for (int it = 0; it < kProbeItems; ++it) {
             const int64_t r = base + (int64_t)it * kProbeThreads + threadIdx.x;
+            const InKey kraw = knext;
+            rn = it + 1 < kProbeItems ? r + kProbeThreads : base + grid_round + threadIdx.x;
+            if (rn < n) knext = __ldcs(keys + rn);
             bool active = r < n;
             uint32_t k = 0, slot = 0, steps = 0;
             if (active) {
-                const int64_t key = (int64_t)__ldcs(keys + r);
+                const int64_t key = (int64_t)kraw;
                 if (check_range && (key < rng.lo || key > rng.hi)) active = false;
                 k = KeyCodec<uint32_t>::encode(key, rng.offset);
-                slot = mix32(k) & mask;
+                slot = mix32(k) & mask & ~1u;
+            }
+            if (first_match) {
+                // unique build keys: walk the chain alone, two slots per load
+                uint32_t bi = 0;
+                bool hit = false;
+                if (active) {
+                    for (uint32_t step = 0;; step += 2) {
+                        const ulonglong2 v = ld_keep2(reinterpret_cast<const ulonglong2*>(table + slot), keep);
+                        if (v.x == kEmptySlot) break;
+                        if ((uint32_t)(v.x >> 32) == k) {
+                            hit = true;
+                            bi = (uint32_t)v.x;
+                            break;
+                        }
+                        if (v.y == kEmptySlot) break;
+                        if ((uint32_t)(v.y >> 32) == k) {
+                            hit = true;
+                            bi = (uint32_t)v.y;
+                            break;
+                        }
+                        if (step + 2 > mask) {
+                            atomicOr(&ctrl->err, kErrTableFull);
+                            break;
+                        }
+                        slot = (slot + 2) & mask;
+                    }
+                }
+                emit<AGG, kStage>(st, agg, hit, bi, (uint32_t)r, out, &ctrl->cursor);
+                continue;
             }
             while (__any_sync(0xffffffffu, active)) {
                 bool hit = false;
                 uint32_t bi = 0;
                 if (active) {
-                    const unsigned long long s = __ldg(table + slot);
+                    const unsigned long long s = ld_keep(table + slot, keep);
                     if (s == kEmptySlot) {
                         active = false;
                     } else {
@@ -130,16 +185,23 @@ __global__ void __launch_bounds__(kProbeThreads)
     if (threadIdx.x == 0) st.count = 0;
     __syncthreads();
     AggState agg{0ull, 0ull};
+    const uint64_t keep = l2_keep_policy();  // the table stays in L2 while keys and pairs stream
     const int64_t round = (int64_t)kProbeThreads * kProbeItems;
-    for (int64_t base = (int64_t)blockIdx.x * round; base < n; base += (int64_t)gridDim.x * round) {
+    const int64_t grid_round = (int64_t)gridDim.x * round;
+    int64_t rn = (int64_t)blockIdx.x * round + threadIdx.x;
+    int64_t knext = rn < n ? __ldcs(keys + rn) : 0;
+    for (int64_t base = (int64_t)blockIdx.x * round; base < n; base += grid_round) {
 #pragma unroll 1
         for (int it = 0; it < kProbeItems; ++it) {
             const int64_t r = base + (int64_t)it * kProbeThreads + threadIdx.x;
+            const int64_t kraw = knext;
+            rn = it + 1 < kProbeItems ? r + kProbeThreads : base + grid_round + threadIdx.x;
+            if (rn < n) knext = __ldcs(keys + rn);
             bool active = r < n;
             uint64_t k = 0;
             unsigned long long slot = 0, steps = 0;
             if (active) {
-                const int64_t key = __ldcs(keys + r);
+                const int64_t key = kraw;
                 if (check_range && (key < rng.lo || key > rng.hi)) active = false;
                 k = (uint64_t)key;
                 slot = mix64(k) & mask;
@@ -148,7 +210,7 @@ __global__ void __launch_bounds__(kProbeThreads)
                 bool hit = false;
                 uint32_t bi = 0;
                 if (active) {
-                    const ulonglong2 s = __ldg(reinterpret_cast<const ulonglong2*>(table + slot));
+                    const ulonglong2 s = ld_keep2(reinterpret_cast<const ulonglong2*>(table + slot), keep);
                     if (s.y == kEmptySlot) {
                         active = false;
                     } else {
@@ -242,12 +304,12 @@ cudaError_t nphj_run(const JoinArgs& a, const PlanDev& plan, const NphjScratch& 
                 auto kern = agg ? nphj_probe_packed<int32_t, true> : nphj_probe_packed<int32_t, false>;
                 kern<<<probe_grid(kern, a.np, di), kProbeThreads, 0, stream>>>(
                     static_cast<const int32_t*>(a.pkeys), a.np, plan.range, plan.check_range, table,
-                    mask, out, ctrl);
+                    mask, out, ctrl, plan.variant != EIGER_STATIC);
             } else {
                 auto kern = agg ? nphj_probe_packed<int64_t, true> : nphj_probe_packed<int64_t, false>;
                 kern<<<probe_grid(kern, a.np, di), kProbeThreads, 0, stream>>>(
                     static_cast<const int64_t*>(a.pkeys), a.np, plan.range, plan.check_range, table,
-                    mask, out, ctrl);
+                    mask, out, ctrl, plan.variant != EIGER_STATIC);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }

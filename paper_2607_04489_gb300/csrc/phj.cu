@@ -293,8 +293,8 @@ __device__ __forceinline__ void flush_positional(Stage<kJoinStage>& st, uint32_t
         if (ball[j] & (1u << lane)) {
             const unsigned long long pos = base + s_grp[j * kJoinWarps + w] + __popc(ball[j] & lt);
             if (PAIRS && fits) {
-                out.bidx[pos] = st.b[i];
-                out.pidx[pos] = st.p[i];
+                __stcs(out.bidx + pos, st.b[i]);
+                __stcs(out.pidx + pos, st.p[i]);
             } else {
                 write_match(out, pos, st.b[i], st.p[i]);
             }
