@@ -768,7 +768,8 @@ def run_star(args):
     int32 keys, int64 payloads), 600M fact rows (uniform or Zipf(--theta)
     foreign keys, 10 % absent), filtered to --selectivity; one step is
     eiger_join_sum (the exact sum of matched dimension + fact payloads), AUTO
-    against the static join."""
+    (payloads carried through the partitioning) against the same plan with
+    the payloads gathered by tuple ID and against the static join."""
     import torch
 
     from paper_2607_04489_gb300 import eiger, workloads
@@ -783,12 +784,15 @@ def run_star(args):
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def arm(variant, profile=False):
-        ws = torch.empty(eiger.join_workspace(nd, nf, eiger.I32, variant), dtype=torch.uint8, device=dev)
+    pay_bytes = w.build_pay.element_size()
+
+    def arm(variant, profile=False, mat="auto"):
+        ws = torch.empty(eiger.join_sum_workspace(nd, nf, eiger.I32, pay_bytes, variant, mat),
+                         dtype=torch.uint8, device=dev)
         res = None
         for _ in range(args.warmup):
             res = eiger.join_sum(w.build_keys, w.build_pay, w.probe_keys, w.probe_pay, variant=variant,
-                                 workspace=ws, stream=stream)
+                                 materialize=mat, workspace=ws, stream=stream)
         stages, launches = {}, 0
         if profile:
             eiger.profile(True)
@@ -797,7 +801,7 @@ def run_star(args):
         e0.record(stream)
         for _ in range(args.steps):
             res = eiger.join_sum(w.build_keys, w.build_pay, w.probe_keys, w.probe_pay, variant=variant,
-                                 workspace=ws, stream=stream)
+                                 materialize=mat, workspace=ws, stream=stream)
             if profile:
                 for name, ms, nl, by in eiger.profile_read():
                     st_ = stages.setdefault(name, [0.0, 0.0, 0])
@@ -822,6 +826,9 @@ def run_star(args):
     sms, (stotal, smatches, _), _, _ = arm("static")
     if (stotal, smatches) != (total, matches):
         raise RuntimeError("static and adaptive sums differ")
+    gms, (gtotal, gmatches, _), _, _ = arm("auto", mat="gfur")
+    if (gtotal, gmatches) != (total, matches):
+        raise RuntimeError("gathered and carried sums differ")
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     rows = stage_table(stages)
@@ -834,9 +841,11 @@ def run_star(args):
                                    "exact sum of matched payloads",
                        "dim_rows": nd, "fact_rows": nf, "matches": matches,
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2; no flush"},
-            "plan": {"variant": plan.variant, "bits1": plan.bits1, "bits2": plan.bits2},
+            "plan": {"variant": plan.variant, "bits1": plan.bits1, "bits2": plan.bits2,
+                     "materialize": plan.materialize},
             "static": {"ms_per_step": sms, "value": tuples / (sms * 1e-3), "unit": "tuples/s",
                        "speedup_of_adaptive": sms / ms},
+            "arms": {"auto_plan_gfur": {"ms_per_step": gms, "value": tuples / (gms * 1e-3), "unit": "tuples/s"}},
             "roofline": {"bound": "hbm", "kernel": dom["stage"], "achieved": dom["gbs"], "peak": hbm,
                          "peak_source": peak_src, "unit": "GB/s", "frac": dom["gbs"] / hbm, "traffic": None,
                          "algorithmic_bytes": dom["bytes"]},

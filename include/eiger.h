@@ -143,10 +143,10 @@ eiger_status eiger_plan(const eiger_stats_t* build, const eiger_stats_t* probe, 
                         int64_t np, eiger_dtype dtype, eiger_plan_t* out);
 
 /*
- * Scratch bytes eiger_join / eiger_join_sum need. `variant` and `knobs` as
- * passed to the join; for EIGER_AUTO (or knobs == NULL with a non-static
- * variant) the result covers every plan the selector can return.
- * Errors: INVALID_ARG.
+ * Scratch bytes eiger_join needs (and eiger_join_sum with EIGER_GFUR).
+ * `variant` and `knobs` as passed to the join; for EIGER_AUTO (or knobs ==
+ * NULL with a non-static variant) the result covers every plan the selector
+ * can return. Errors: INVALID_ARG.
  */
 eiger_status eiger_join_workspace(int64_t nb, int64_t np, eiger_dtype dtype, eiger_variant variant,
                                   const eiger_plan_t* knobs, size_t* bytes);
@@ -183,20 +183,37 @@ eiger_status eiger_join(eiger_dtype dtype, const void* d_bkeys, const void* d_bp
                         eiger_plan_t* plan_used, void* stream);
 
 /*
+ * Scratch bytes eiger_join_sum needs: arguments as passed to it (the
+ * materialisation decides whether the two payload columns are carried).
+ * Errors: INVALID_ARG.
+ */
+eiger_status eiger_join_sum_workspace(int64_t nb, int64_t np, eiger_dtype dtype, int32_t payload_bytes,
+                                      eiger_variant variant, eiger_materialize materialize,
+                                      const eiger_plan_t* knobs, size_t* bytes);
+
+/*
  * eiger_join_sum -- the join fused with an exact aggregate instead of
  * materialised pairs: sum over matches (i, j) of build_pay[i] + probe_pay[j]
  * (payloads sign-extended to 64 bits), accumulated modulo 2^64 and returned as
  * int64; addition modulo 2^64 is exact and order-independent. This is the
  * foreign-key join whose matched payloads are summed (the star-schema workload
- * shape of the TPC-H joins, Sec. 5.7). Payloads are required. Arguments otherwise as eiger_join.
+ * shape of the TPC-H joins, Sec. 5.7). Payloads are required.
+ * materialize: how the payloads reach the sum (Sec. 3.2). EIGER_GFUR reads
+ *          both payloads of every match by tuple ID from the caller's
+ *          columns (any variant). EIGER_GFTR carries both columns through the
+ *          partitioning (PHJ1/PHJ2) or sort (SMJ) passes and reads them by
+ *          position, so the probe side's reads are sequential; rejected for
+ *          NPHJ/STATIC. EIGER_MAT_AUTO takes GFTR for PHJ and SMJ plans.
+ *          plan_used.materialize reports the strategy that ran.
+ * Workspace: eiger_join_sum_workspace. Arguments otherwise as eiger_join.
  * out_sum, out_count: host.
  * Errors: as eiger_join except CAPACITY.
  */
 eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* d_bpay, int64_t nb,
                             const void* d_pkeys, const void* d_ppay, int64_t np,
-                            int32_t payload_bytes, eiger_variant variant, const eiger_plan_t* knobs,
-                            int64_t* out_sum, int64_t* out_count, void* d_workspace,
-                            size_t ws_bytes, eiger_plan_t* plan_used, void* stream);
+                            int32_t payload_bytes, eiger_variant variant, eiger_materialize materialize,
+                            const eiger_plan_t* knobs, int64_t* out_sum, int64_t* out_count,
+                            void* d_workspace, size_t ws_bytes, eiger_plan_t* plan_used, void* stream);
 
 /* ------------------------------------------------------------------------
  * Wide joins: several payload columns per side (Sec. 3.2 materialisation;

@@ -351,8 +351,8 @@ void sort_passes(eiger_plan_t* p) {
 }
 
 // Materialisation that runs: GFTR needs a transformation (partitioning or
-// sorting) and at least one column to carry; the aggregate reads payloads by
-// tuple ID.
+// sorting) and at least one column to carry (the aggregate carries the two
+// summed payload columns).
 eiger_status resolve_materialize(const JoinCall& c, eiger_plan_t* pub) {
     const bool transformed = pub->variant == EIGER_PHJ1 || pub->variant == EIGER_PHJ2 || pub->variant == EIGER_SMJ;
     const bool cols = c.out.b.n + c.out.p.n > 0;
@@ -361,13 +361,14 @@ eiger_status resolve_materialize(const JoinCall& c, eiger_plan_t* pub) {
         return fail(EIGER_ERR_INVALID_ARG, "GFTR needs a partitioned or sort-merge plan (got variant %d)",
                     pub->variant);
     if (m == EIGER_MAT_AUTO) m = transformed ? EIGER_GFTR : EIGER_GFUR;
-    if (!cols || c.out.aggregate) m = EIGER_GFUR;
+    if (!cols) m = EIGER_GFUR;
     pub->materialize = m;
     return EIGER_OK;
 }
 
 void set_carry(PlanDev& d, const JoinOut& out, int materialize) {
     d.gftr = materialize == EIGER_GFTR;
+    d.no_rows = d.gftr && out.aggregate;  // the positional sum needs no tuple IDs
     d.ncols[0] = d.gftr ? out.b.n : 0;
     d.ncols[1] = d.gftr ? out.p.n : 0;
     for (int q = 0; q < kMaxCols; ++q) {
@@ -1040,10 +1041,30 @@ extern "C" eiger_status eiger_join_batched(eiger_dtype dtype, const eiger_join_d
     return EIGER_OK;
 }
 
+eiger_status eiger_join_sum_workspace(int64_t nb, int64_t np, eiger_dtype dtype, int32_t payload_bytes,
+                                      eiger_variant variant, eiger_materialize materialize,
+                                      const eiger_plan_t* knobs, size_t* bytes) {
+    if (!bytes) return fail(EIGER_ERR_INVALID_ARG, "bytes is NULL");
+    if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
+    if (nb < 0 || np < 0 || nb > kMaxRows || np > kMaxRows)
+        return fail(EIGER_ERR_INVALID_ARG, "row counts must be in [0, 2^32)");
+    if (variant < EIGER_AUTO || variant > EIGER_SMJ) return fail(EIGER_ERR_INVALID_ARG, "bad variant");
+    if (materialize < EIGER_GFUR || materialize > EIGER_MAT_AUTO)
+        return fail(EIGER_ERR_INVALID_ARG, "bad materialize");
+    if (payload_bytes != 4 && payload_bytes != 8)
+        return fail(EIGER_ERR_INVALID_ARG, "payload_bytes must be 4 or 8, got %d", payload_bytes);
+    ColSpec cs{};
+    cs.materialize = materialize;
+    cs.n[0] = cs.n[1] = 1;
+    cs.bytes[0][0] = cs.bytes[1][0] = payload_bytes;
+    *bytes = join_workspace_bytes(nb, np, dtype, variant, knobs, cs);
+    return EIGER_OK;
+}
+
 eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* d_bpay, int64_t nb,
                             const void* d_pkeys, const void* d_ppay, int64_t np, int32_t payload_bytes,
-                            eiger_variant variant, const eiger_plan_t* knobs, int64_t* out_sum,
-                            int64_t* out_count, void* d_workspace, size_t ws_bytes,
+                            eiger_variant variant, eiger_materialize materialize, const eiger_plan_t* knobs,
+                            int64_t* out_sum, int64_t* out_count, void* d_workspace, size_t ws_bytes,
                             eiger_plan_t* plan_used, void* stream) {
     if (!out_sum) return fail(EIGER_ERR_INVALID_ARG, "out_sum is NULL");
     if ((nb > 0 && !d_bpay) || (np > 0 && !d_ppay))
@@ -1059,10 +1080,14 @@ eiger_status eiger_join_sum(eiger_dtype dtype, const void* d_bkeys, const void* 
     c.pay_bytes = payload_bytes;
     c.variant = variant;
     c.knobs = knobs;
+    c.materialize = materialize;
+    // one summed column per side: read by tuple ID (GFUR) or carried (GFTR)
     c.out.b.src[0] = d_bpay;
     c.out.b.bytes[0] = payload_bytes;
+    c.out.b.n = 1;
     c.out.p.src[0] = d_ppay;
     c.out.p.bytes[0] = payload_bytes;
+    c.out.p.n = 1;
     c.out.aggregate = 1;
     c.out.capacity = 0;
     c.out_count = out_count;

@@ -638,6 +638,7 @@ cudaError_t gb_part_run(const GbArgs& g, const GbPlanDev& plan, const GbScratch&
     pd.range.hi = INT64_MAX;
     pd.range.offset = plan.offset;
     pd.check_range = 0;
+    pd.no_rows = 1;  // groups are aggregated from the carried columns by position
     ColSide carry{};
     int nc = 0;
     int col_of[kMaxCols];

@@ -71,6 +71,7 @@ struct PlanDev {
     int gftr;         // payload columns travel with the keys (GFTR) instead of being gathered by tuple ID
     int ncols[2];     // GFTR: columns carried per side (build, probe)
     int col_bytes[2][kMaxCols];
+    int no_rows;      // the consumer reads rows by position only: the passes keep no tuple IDs
 };
 
 // Inputs of one join, as given to eiger_join.

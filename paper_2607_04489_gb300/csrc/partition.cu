@@ -85,21 +85,6 @@ __device__ __forceinline__ size_t count_index(const Tile& tl, uint32_t t, uint32
     return ((size_t)tl.tile_base << bits) + (size_t)d * tl.ntiles_seg + (t - tl.tile_base);
 }
 
-template <typename InKey, typename KeyT, bool FIRST>
-__device__ __forceinline__ bool part_load(const PartPass<InKey, KeyT>& a, uint32_t r, KeyT& k,
-                                          uint32_t& id) {
-    if (FIRST) {
-        const int64_t key = (int64_t)__ldcs(a.raw + r);
-        if (a.check_range && (key < a.rng.lo || key > a.rng.hi)) return false;
-        k = KeyCodec<KeyT>::encode(key, a.rng.offset);
-        id = r;
-    } else {
-        k = __ldcs(a.in_key + r);
-        id = __ldcs(a.in_idx + r);
-    }
-    return true;
-}
-
 // Partition digit: bits of the mixed key (hash partitioning) or, for the
 // sort, bits of the encoded key itself.
 template <bool SORTM, typename KeyT>
@@ -225,6 +210,22 @@ struct TileRing {
 template <typename E>
 __device__ __forceinline__ uint32_t lead_of(const E* first) {
     return (uint32_t)((reinterpret_cast<uintptr_t>(first) & 15u) / sizeof(E));
+}
+
+// Warp 0: start loading tile `tl` of a scatter pass into buffer b. Later passes
+// load the tile's tuple IDs too, unless the side keeps none (in_idx == nullptr:
+// its consumer reads rows by position only).
+template <typename InKey, typename KeyT, bool FIRST>
+__device__ __forceinline__ void issue_tile(const TileRing<InKey, KeyT, FIRST>& ring,
+                                           const PartPass<InKey, KeyT>& a, const Tile& tl, int b) {
+    if constexpr (FIRST) {
+        ring.template issue<false>(a, tl, b);
+    } else {
+        if (a.in_idx)
+            ring.template issue<true>(a, tl, b);
+        else
+            ring.template issue<false>(a, tl, b);
+    }
 }
 
 // Decodes element e of the current tile: applies the range test and the
@@ -369,6 +370,23 @@ __device__ __forceinline__ void carry_column(const V* __restrict__ src, V* __res
     __syncthreads();
 }
 
+// Every thread: asks L2 to fetch the carried columns of tile `tl` (one
+// 128-byte line per thread and step), a tile ahead of carry_columns reading
+// them, so the carry does not wait on DRAM. Addresses stay inside the tile.
+// Used in later passes only: measured on GB300, it cut the pass-2 scatters by
+// 0.1-0.3 ms but slowed the pass-1 scatters (which stream the caller's
+// columns beside the TMA key loads) by 0.7-1.0 ms on the wide, group-by and
+// star workloads.
+__device__ __forceinline__ void prefetch_columns(const ColCarry& cc, const Tile& tl) {
+#pragma unroll 1
+    for (int c = 0; c < cc.n; ++c) {
+        const char* base = static_cast<const char*>(cc.in[c]) + (size_t)tl.start * cc.bytes[c];
+        const uint32_t bytes = tl.len * (uint32_t)cc.bytes[c];
+        for (uint32_t off = threadIdx.x * 128u; off < bytes; off += blockDim.x * 128u)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
+    }
+}
+
 template <bool SORTM, typename DigT>
 __device__ __forceinline__ void carry_columns(const ColCarry& cc, uint32_t tstart, const uint32_t (&dr)[kPartItems],
                                               const uint16_t* s_wc, uint32_t nd, const uint32_t* s_start,
@@ -394,6 +412,7 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
     __shared__ uint32_t s_warp[kPartThreads / kWarp];
     __shared__ uint32_t s_kept;
     const uint32_t nd = 1u << a.bits;
+    const bool rows = a.out_idx != nullptr;  // tuple IDs travel with the keys
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + 16);
     uint32_t* s_start = s_cnt + nd;
     uint32_t* s_goff = s_start + nd;
@@ -421,14 +440,14 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
     }
     Tile d_next{};  // warp 0: descriptor of the next tile to issue, loaded one tile early
     if (threadIdx.x < kWarp) {
-        if (t < ntiles) ring.template issue<!FIRST>(a, tl_cur, 0);
+        if (t < ntiles) issue_tile(ring, a, tl_cur, 0);
         if (t + gridDim.x < ntiles) d_next = get_tile(a, t + gridDim.x);
     }
     for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
         const int b = it & 1;
         const uint32_t tn = t + gridDim.x;
         if (threadIdx.x < kWarp && tn < ntiles) {
-            ring.template issue<!FIRST>(a, d_next, b ^ 1);
+            issue_tile(ring, a, d_next, b ^ 1);
             if (tn + gridDim.x < ntiles) d_next = get_tile(a, tn + gridDim.x);
         }
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
@@ -445,6 +464,8 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
         const Tile tl = tl_cur;
         if (tn < ntiles) {  // next tile's offsets, consumed next iteration
             tl_cur = get_tile(a, tn);
+            if constexpr (!FIRST)
+                if (a.cc.n) prefetch_columns(a.cc, tl_cur);
 #pragma unroll
             for (int q = 0; q < kGoffPerThread; ++q) {
                 const uint32_t d = threadIdx.x + q * kPartThreads;
@@ -453,7 +474,8 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
         }
         const auto* kbuf = ring.keys(b) + lead_of(Ring::key_src(a, tl.start));
         const uint32_t* rbuf = nullptr;
-        if constexpr (!FIRST) rbuf = ring.rows(b) + lead_of(a.in_idx + tl.start);
+        if constexpr (!FIRST)
+            if (rows) rbuf = ring.rows(b) + lead_of(a.in_idx + tl.start);
 
         KeyT kk[kPartItems];
         uint32_t dr[kPartItems];  // (rank << 12) | digit, or kNoDigit
@@ -482,10 +504,7 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
                 const uint32_t pos = s_start[d] + (dr[j] >> 12);
                 s_key[pos] = kk[j];
                 s_dig[pos] = (uint16_t)d;
-                if constexpr (FIRST)
-                    s_idx[pos] = tl.start + e;
-                else
-                    s_idx[pos] = rbuf[e];
+                if (rows) s_idx[pos] = FIRST ? tl.start + e : rbuf[e];
             }
         }
         __syncthreads();
@@ -495,7 +514,7 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
             const uint32_t d = s_dig[pos];
             const uint32_t g = s_goff[d] + pos;
             a.out_key[g] = s_key[pos];
-            a.out_idx[g] = s_idx[pos];
+            if (rows) a.out_idx[g] = s_idx[pos];
         }
         __syncthreads();
         // carried columns reuse the key and row staging (contiguous, >= 8 bytes per row)
@@ -528,6 +547,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
     __shared__ uint32_t s_warp[kPartThreads / kWarp];
     __shared__ uint32_t s_kept;
     const uint32_t nd = 1u << a.bits;
+    const bool rows = a.out_idx != nullptr;  // tuple IDs travel with the keys
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + 16);
     uint32_t* s_start = s_cnt + nd;
     uint32_t* s_goff = s_start + nd;
@@ -556,14 +576,14 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
     }
     Tile d_next{};  // warp 0: descriptor of the next tile to issue, loaded one tile early
     if (threadIdx.x < kWarp) {
-        if (t < ntiles) ring.template issue<!FIRST>(a, tl_cur, 0);
+        if (t < ntiles) issue_tile(ring, a, tl_cur, 0);
         if (t + gridDim.x < ntiles) d_next = get_tile(a, t + gridDim.x);
     }
     for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
         const int b = it & 1;
         const uint32_t tn = t + gridDim.x;
         if (threadIdx.x < kWarp && tn < ntiles) {
-            ring.template issue<!FIRST>(a, d_next, b ^ 1);
+            issue_tile(ring, a, d_next, b ^ 1);
             if (tn + gridDim.x < ntiles) d_next = get_tile(a, tn + gridDim.x);
         }
         for (uint32_t d = lane; d < nd; d += kWarp) s_wc[w * nd + d] = 0;
@@ -580,6 +600,8 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
         const Tile tl = tl_cur;
         if (tn < ntiles) {
             tl_cur = get_tile(a, tn);
+            if constexpr (!FIRST)
+                if (a.cc.n) prefetch_columns(a.cc, tl_cur);
 #pragma unroll
             for (int q = 0; q < kGoffPerThread; ++q) {
                 const uint32_t d = threadIdx.x + q * kPartThreads;
@@ -588,7 +610,8 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
         }
         const auto* kbuf = ring.keys(b) + lead_of(Ring::key_src(a, tl.start));
         const uint32_t* rbuf = nullptr;
-        if constexpr (!FIRST) rbuf = ring.rows(b) + lead_of(a.in_idx + tl.start);
+        if constexpr (!FIRST)
+            if (rows) rbuf = ring.rows(b) + lead_of(a.in_idx + tl.start);
 
         KeyT kk[kPartItems];
         uint32_t dr[kPartItems];  // (rank within this warp's rows << 12) | digit, or kNoDigit
@@ -629,10 +652,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
                 const uint32_t pos = s_start[d] + s_wc[w * nd + d] + (dr[j] >> 12);
                 s_key[pos] = kk[j];
                 s_dig[pos] = (uint8_t)d;
-                if constexpr (FIRST)
-                    s_idx[pos] = tl.start + e;
-                else
-                    s_idx[pos] = rbuf[e];
+                if (rows) s_idx[pos] = FIRST ? tl.start + e : rbuf[e];
             }
         }
         __syncthreads();
@@ -641,7 +661,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) sort_scatter_kernel(PartPass<
             const uint32_t d = s_dig[pos];
             const uint32_t g = s_goff[d] + pos;
             a.out_key[g] = s_key[pos];
-            a.out_idx[g] = s_idx[pos];
+            if (rows) a.out_idx[g] = s_idx[pos];
         }
         __syncthreads();
         if (a.cc.n) carry_columns<true>(a.cc, tl.start, dr, s_wc, nd, s_start, s_goff, s_dig, nk, s_key);
@@ -859,8 +879,8 @@ inline double carry_bytes(const ColCarry& cc) {
 
 // One partitioning (or sort) pass over n rows. Algorithmic bytes per launch:
 // the histogram reads each key once; the scatter reads each (key, row) once
-// and writes each kept (key', row) once, plus the carried columns; the scan
-// reads and writes the counts.
+// and writes each kept (key', row) once (keys alone when the side keeps no
+// tuple IDs), plus the carried columns; the scan reads and writes the counts.
 template <typename InKey, typename KeyT, bool FIRST, bool SORTM>
 cudaError_t run_pass(PartPass<InKey, KeyT> a, size_t max_tiles, const PartSide& s, uint32_t* total,
                      unsigned* err, const DevInfo& di, cudaStream_t stream, const char* side_name, int pass_no) {
@@ -874,7 +894,8 @@ cudaError_t run_pass(PartPass<InKey, KeyT> a, size_t max_tiles, const PartSide& 
     if ((e = set_smem(scat, ssmem)) != cudaSuccess) return e;
     const double n = (double)a.n;
     const double in_key = FIRST ? (double)sizeof(InKey) : (double)sizeof(KeyT);
-    const double tuple = (double)(sizeof(KeyT) + sizeof(uint32_t));
+    const double row = a.out_idx ? (double)sizeof(uint32_t) : 0.0;  // tuple IDs, when the side keeps them
+    const double tuple = (double)sizeof(KeyT) + row;
     const double in_tuple = FIRST ? (double)sizeof(InKey) : tuple;
     const char* kind = SORTM ? "sort" : "part";
     char name[32];
@@ -921,7 +942,7 @@ cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanD
     PartPass<InKey, KeyT> a{};
     a.raw = keys;
     a.out_key = static_cast<KeyT*>(s.key[0]);
-    a.out_idx = s.idx[0];
+    a.out_idx = plan.no_rows ? nullptr : s.idx[0];
     a.n = n;
     a.rng = plan.range;
     a.check_range = side == 1 ? plan.check_range : 0;
@@ -945,9 +966,9 @@ cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanD
         }
         PartPass<InKey, KeyT> b{};
         b.in_key = static_cast<const KeyT*>(s.key[0]);
-        b.in_idx = s.idx[0];
+        b.in_idx = plan.no_rows ? nullptr : s.idx[0];
         b.out_key = static_cast<KeyT*>(s.key[1]);
-        b.out_idx = s.idx[1];
+        b.out_idx = plan.no_rows ? nullptr : s.idx[1];
         b.n = n;
         b.rng = plan.range;
         b.check_range = 0;
@@ -986,7 +1007,7 @@ cudaError_t sort_typed(const InKey* keys, uint32_t n, int side, const PlanDev& p
     PartPass<InKey, KeyT> a{};
     a.raw = keys;
     a.out_key = static_cast<KeyT*>(s.key[0]);
-    a.out_idx = s.idx[0];
+    a.out_idx = plan.no_rows ? nullptr : s.idx[0];
     a.n = n;
     a.rng = plan.range;
     a.check_range = side == 1 ? plan.check_range : 0;
@@ -1008,9 +1029,9 @@ cudaError_t sort_typed(const InKey* keys, uint32_t n, int side, const PlanDev& p
     for (int i = 1; i < passes; ++i) {
         PartPass<InKey, KeyT> b{};
         b.in_key = static_cast<const KeyT*>(s.key[(i - 1) & 1]);
-        b.in_idx = s.idx[(i - 1) & 1];
+        b.in_idx = plan.no_rows ? nullptr : s.idx[(i - 1) & 1];
         b.out_key = static_cast<KeyT*>(s.key[i & 1]);
-        b.out_idx = s.idx[i & 1];
+        b.out_idx = plan.no_rows ? nullptr : s.idx[i & 1];
         b.n = n;
         b.rng = plan.range;
         b.check_range = 0;

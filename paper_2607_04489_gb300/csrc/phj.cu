@@ -504,13 +504,20 @@ cudaError_t launch_join(const PhjScratch& s, const PlanDev& plan, const JoinOut&
     a.P = 1u << (plan.bits1 + (passes == 2 ? plan.bits2 : 0));
     const bool pairs = !out.aggregate && out.bidx && out.pidx && out.b.n == 0 && out.p.n == 0 && !out.b.rowmap &&
                        !out.p.rowmap;
-    auto kern = out.aggregate ? phj_join_kernel<KeyT, true, false, false>
+    auto kern = out.aggregate ? (plan.gftr ? phj_join_kernel<KeyT, true, false, true>
+                                           : phj_join_kernel<KeyT, true, false, false>)
                 : pairs       ? phj_join_kernel<KeyT, false, true, false>
                 : plan.gftr   ? phj_join_kernel<KeyT, false, false, true>
                               : phj_join_kernel<KeyT, false, false, false>;
-    // reads every partitioned (key', row) of both sides once, writes the matches
+    // reads every partitioned (key', row) of both sides once, writes the matches;
+    // the positional aggregate reads keys only, each carried build payload at
+    // most once and the probe payload of every match
     const double tuple = (double)(sizeof(KeyT) + sizeof(uint32_t));
-    ProfScope ps("phj_join", tuple * (double)(nb + np), stream, match_bytes(out));
+    const bool pos_agg = out.aggregate && plan.gftr;
+    ProfScope ps("phj_join",
+                 pos_agg ? (double)sizeof(KeyT) * (double)(nb + np) + (double)out.b.bytes[0] * (double)nb
+                         : tuple * (double)(nb + np),
+                 stream, pos_agg ? (double)out.p.bytes[0] : match_bytes(out));
     const size_t smem = join_smem<KeyT>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

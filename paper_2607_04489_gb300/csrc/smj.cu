@@ -234,7 +234,7 @@ cudaError_t launch_smj(const SmjScratch& s, const PlanDev& plan, const JoinOut& 
         smj_window_kernel<KeyT><<<(nch + 255) / 256, 256, 0, stream>>>(a, s.window);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    auto kern = out.aggregate ? smj_join_kernel<KeyT, true, false>
+    auto kern = out.aggregate ? (plan.gftr ? smj_join_kernel<KeyT, true, true> : smj_join_kernel<KeyT, true, false>)
                 : plan.gftr   ? smj_join_kernel<KeyT, false, true>
                               : smj_join_kernel<KeyT, false, false>;
     const size_t smem = smj_smem<KeyT>();

@@ -178,7 +178,7 @@ SYMBOLS = ("eiger_stats_workspace", "eiger_stats", "eiger_plan", "eiger_join_wor
            "eiger_mlp_adam", "eiger_features", "eiger_class_plan", "eiger_selector_set",
            "eiger_join_static_noalloc", "eiger_profile", "eiger_profile_read", "eiger_last_error",
            "eiger_version", "eiger_join_wide_workspace", "eiger_join_wide", "eiger_groupby_workspace",
-           "eiger_groupby")
+           "eiger_groupby", "eiger_join_sum_workspace")
 MLP_IN, MLP_HIDDEN, MLP_OUT = 12, 64, 15
 
 
@@ -209,9 +209,12 @@ def load():
     lib.eiger_join.argtypes = [c.c_int, vp, vp, i64, vp, vp, i64, i32, c.c_int, c.POINTER(PlanT),
                                vp, vp, vp, vp, i64, c.POINTER(i64), vp, sz, c.POINTER(PlanT), vp]
     lib.eiger_join_sum.restype = c.c_int
-    lib.eiger_join_sum.argtypes = [c.c_int, vp, vp, i64, vp, vp, i64, i32, c.c_int,
+    lib.eiger_join_sum.argtypes = [c.c_int, vp, vp, i64, vp, vp, i64, i32, c.c_int, c.c_int,
                                    c.POINTER(PlanT), c.POINTER(i64), c.POINTER(i64), vp, sz,
                                    c.POINTER(PlanT), vp]
+    lib.eiger_join_sum_workspace.restype = c.c_int
+    lib.eiger_join_sum_workspace.argtypes = [i64, i64, c.c_int, i32, c.c_int, c.c_int, c.POINTER(PlanT),
+                                             c.POINTER(sz)]
     lib.eiger_join_wide_workspace.restype = c.c_int
     lib.eiger_join_wide_workspace.argtypes = [i64, i64, c.c_int, c.POINTER(ColumnsT), c.POINTER(ColumnsT),
                                               c.c_int, c.c_int, c.POINTER(PlanT), c.POINTER(sz)]
@@ -420,7 +423,16 @@ def join(build_keys: torch.Tensor, probe_keys: torch.Tensor, *, build_pay=None, 
     return JoinResult(n, cut(ob), cut(op), cut(obp), cut(opp), used)
 
 
-def join_sum(build_keys, build_pay, probe_keys, probe_pay, *, variant="auto",
+def join_sum_workspace(nb: int, np_: int, dtype: int, payload_bytes: int, variant="auto",
+                       materialize="auto", knobs: Plan | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    k = knobs.to_c() if knobs is not None else None
+    _check(load().eiger_join_sum_workspace(nb, np_, dtype, payload_bytes, _variant(variant), _mat(materialize),
+                                           ctypes.byref(k) if k is not None else None, ctypes.byref(out)))
+    return out.value
+
+
+def join_sum(build_keys, build_pay, probe_keys, probe_pay, *, variant="auto", materialize="auto",
              knobs: Plan | None = None, workspace: torch.Tensor | None = None, stream=None):
     """eiger_join_sum: (sum over matches of build_pay + probe_pay mod 2^64, |J|, plan)."""
     lib = load()
@@ -431,14 +443,15 @@ def join_sum(build_keys, build_pay, probe_keys, probe_pay, *, variant="auto",
     if bp.dtype != pp.dtype:
         raise TypeError("payload columns must share a dtype")
     if workspace is None:
-        workspace = torch.empty(join_workspace(bk.numel(), pk.numel(), dt, variant, knobs),
+        workspace = torch.empty(join_sum_workspace(bk.numel(), pk.numel(), dt, bp.element_size(), variant,
+                                                   materialize, knobs),
                                 dtype=torch.uint8, device=dev)
     s = ctypes.c_int64(0)
     cnt = ctypes.c_int64(0)
     used = PlanT()
     k = knobs.to_c() if knobs is not None else None
     _check(lib.eiger_join_sum(dt, _ptr(bk), _ptr(bp), bk.numel(), _ptr(pk), _ptr(pp), pk.numel(),
-                              bp.element_size(), _variant(variant),
+                              bp.element_size(), _variant(variant), _mat(materialize),
                               ctypes.byref(k) if k is not None else None, ctypes.byref(s),
                               ctypes.byref(cnt), _ptr(workspace), workspace.numel(),
                               ctypes.byref(used), _stream(stream)))

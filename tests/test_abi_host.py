@@ -130,8 +130,13 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     # sum without payloads
     s = ctypes.c_int64(0)
     st = so.eiger_join_sum(lib.I32, ctypes.c_void_p(64), None, 3, ctypes.c_void_p(64), None, 3, 8, 0,
-                           None, ctypes.byref(s), ctypes.byref(cnt), None, 0, None, None)
+                           lib.MAT_AUTO, None, ctypes.byref(s), ctypes.byref(cnt), None, 0, None, None)
     assert st == lib.ERR_INVALID_ARG
+    # bad materialisation
+    st = so.eiger_join_sum(lib.I32, ctypes.c_void_p(64), ctypes.c_void_p(64), 3, ctypes.c_void_p(64),
+                           ctypes.c_void_p(64), 3, 8, 0, 5, None, ctypes.byref(s), ctypes.byref(cnt), None, 0,
+                           None, None)
+    assert st == lib.ERR_INVALID_ARG and "materialize" in lib.last_error()
     # stats: NULL output, negative n
     assert so.eiger_stats(None, 0, lib.I32, None, None, 0, None) == lib.ERR_INVALID_ARG
     out = lib.StatsT()
@@ -191,6 +196,24 @@ def test_wide_workspace_counts_carried_columns(lib):
     assert smj >= 2 * (nb * 12 + np_ * 8)
     assert lib.join_wide_workspace(nb, np_, lib.I64, [], [], "smj", "gfur", None) == \
         lib.join_workspace(nb, np_, lib.I64, "smj")
+
+
+def test_sum_workspace_counts_carried_payloads(lib):
+    """A carried (GFTR) sum holds two copies of both payload columns; GFUR
+    needs no more than the plain join."""
+    nb, np_ = 1 << 20, 1 << 22
+    knobs = lib.Plan("phj2", 5, 5, 1)
+    gfur = lib.join_sum_workspace(nb, np_, lib.I32, 8, "phj2", "gfur", knobs)
+    gftr = lib.join_sum_workspace(nb, np_, lib.I32, 8, "phj2", "gftr", knobs)
+    assert gfur == lib.join_workspace(nb, np_, lib.I32, "phj2", knobs)
+    assert gftr - gfur >= 2 * 8 * (nb + np_)
+    assert lib.join_sum_workspace(nb, np_, lib.I32, 8, "auto", "auto") >= gftr - gfur
+    # NPHJ never carries
+    assert lib.join_sum_workspace(nb, np_, lib.I32, 8, "nphj", "auto") == lib.join_workspace(nb, np_, lib.I32, "nphj")
+    so = lib.load()
+    ws = ctypes.c_size_t(0)
+    assert so.eiger_join_sum_workspace(10, 10, lib.I32, 2, 0, lib.MAT_AUTO, None, ctypes.byref(ws)) == lib.ERR_INVALID_ARG
+    assert so.eiger_join_sum_workspace(10, 10, lib.I32, 8, 0, 3, None, ctypes.byref(ws)) == lib.ERR_INVALID_ARG
 
 
 def test_wide_argument_checks(lib):

@@ -231,10 +231,11 @@ def test_payload_materialisation(eiger, oracle_mod):
         assert r.count == oracle_mod.join_count(bk, pk)
 
 
+@pytest.mark.parametrize("mat", ["auto", "gfur"])
 @pytest.mark.parametrize("variant,kn", [("auto", None), ("nphj", None), ("static", None),
                                         ("phj1", ("phj1", 5, 0, 1)), ("phj2", ("phj2", 4, 4, 1)),
                                         ("smj", None), ("smj", ("smj", 5, 0, 1))])
-def test_join_sum_parity(eiger, oracle_mod, variant, kn):
+def test_join_sum_parity(eiger, oracle_mod, variant, kn, mat):
     rng = np.random.default_rng(31)
     n_dim, n_fact = 30_000, 200_000
     dk = (rng.permutation(n_dim) + 1).astype(np.int32)
@@ -244,10 +245,41 @@ def test_join_sum_parity(eiger, oracle_mod, variant, kn):
     fp = rng.integers(0, 10**7, size=n_fact).astype(np.int64)
     s, c = oracle_mod.join_sum(dk, dp, fk, fp)
     knobs = eiger.Plan(*kn) if kn else None
-    gs, gc, _ = eiger.join_sum(torch.from_numpy(dk).cuda(), torch.from_numpy(dp).cuda(),
-                               torch.from_numpy(fk).cuda(), torch.from_numpy(fp).cuda(),
-                               variant=variant, knobs=knobs)
+    gs, gc, plan = eiger.join_sum(torch.from_numpy(dk).cuda(), torch.from_numpy(dp).cuda(),
+                                  torch.from_numpy(fk).cuda(), torch.from_numpy(fp).cuda(),
+                                  variant=variant, knobs=knobs, materialize=mat)
     assert (gs, gc) == (s, c)
+    carried = mat == "auto" and plan.variant in ("phj1", "phj2", "smj")
+    assert plan.materialize == ("gftr" if carried else "gfur")
+
+
+@pytest.mark.parametrize("pay", [np.int32, np.int64])
+@pytest.mark.parametrize("mat", ["gftr", "gfur"])
+@pytest.mark.parametrize("kn", [("phj1", 1, 0, 0), ("phj2", 1, 1, 1), ("phj2", 3, 3, 0), ("smj", 6, 0, 1)])
+def test_join_sum_duplicates_carried_and_gathered(eiger, oracle_mod, kn, mat, pay):
+    """Duplicate-heavy int64 keys (2000 build rows per key, so the general
+    probe path runs and 1-bit partitions hold several build chunks), 4- and
+    8-byte payloads spanning the full range so the sum wraps: carrying the
+    payloads (GFTR) and gathering them by tuple ID (GFUR) give the oracle's
+    sum and count."""
+    rng = np.random.default_rng(32)
+    bk = rng.integers(0, 10, size=20_000).astype(I64) * 1_000_003 - 7
+    pk = rng.integers(-2, 12, size=30_000).astype(I64) * 1_000_003 - 7
+    info = np.iinfo(pay)
+    bp = rng.integers(info.min, info.max, size=bk.size, dtype=np.int64).astype(pay)
+    pp = rng.integers(info.min, info.max, size=pk.size, dtype=np.int64).astype(pay)
+    s, c = oracle_mod.join_sum(bk, bp, pk, pp)
+    gs, gc, plan = eiger.join_sum(torch.from_numpy(bk).cuda(), torch.from_numpy(bp).cuda(),
+                                  torch.from_numpy(pk).cuda(), torch.from_numpy(pp).cuda(),
+                                  variant=kn[0], knobs=eiger.Plan(*kn), materialize=mat)
+    assert (gs, gc) == (s, c)
+    assert plan.materialize == mat
+
+
+def test_join_sum_gftr_rejected_without_partitioning(eiger):
+    k = torch.arange(100, dtype=torch.int32, device="cuda")
+    with pytest.raises(eiger.EigerError, match="GFTR"):
+        eiger.join_sum(k, k.long(), k, k.long(), variant="nphj", materialize="gftr")
 
 
 def test_capacity_errors_and_retry(eiger, oracle_mod):

@@ -43,10 +43,12 @@ def test_star_schema_sum_and_pairs_parity_reduced(eiger, oracle_mod, theta, sel)
     dk, dp, fk, fp = (t.numpy() for t in (w.build_keys, w.build_pay, w.probe_keys, w.probe_pay))
     s, c = oracle_mod.join_sum(dk, dp, fk, fp)
     assert (s, c) == _direct_sum(dk, dp, fk, fp)
-    for variant, knobs in (("auto", None), ("static", None), ("phj2", eiger.Plan("phj2", 4, 4, 1))):
+    for variant, knobs, mat in (("auto", None, "auto"), ("static", None, "auto"),
+                                ("phj2", eiger.Plan("phj2", 4, 4, 1), "gftr"),
+                                ("phj2", eiger.Plan("phj2", 4, 4, 1), "gfur"), ("smj", None, "gftr")):
         gs, gc, _ = eiger.join_sum(w.build_keys, w.build_pay, w.probe_keys, w.probe_pay,
-                                   variant=variant, knobs=knobs)
-        assert (gs, gc) == (s, c), variant
+                                   variant=variant, knobs=knobs, materialize=mat)
+        assert (gs, gc) == (s, c), (variant, mat)
     eb, ep, n = oracle_mod.join(dk, fk)
     r = eiger.join(w.build_keys, w.probe_keys, variant="auto")
     assert r.count == n
@@ -59,7 +61,8 @@ def test_star_schema_sum_and_pairs_parity_reduced(eiger, oracle_mod, theta, sel)
 
 def test_star_schema_full_size_sum(eiger):
     """150M dimension rows x 600M fact rows, Zipf 1.0 fact keys, no filter:
-    AUTO and the static join both give the exact sum and match count."""
+    AUTO (payloads carried), AUTO with payloads gathered by tuple ID, and the
+    static join all give the exact sum and match count."""
     from paper_2607_04489_gb300 import workloads
 
     free, _ = torch.cuda.mem_get_info()
@@ -69,7 +72,12 @@ def test_star_schema_full_size_sum(eiger):
     expect = _direct_sum(w.build_keys.cpu().numpy(), w.build_pay.cpu().numpy(),
                          w.probe_keys.cpu().numpy(), w.probe_pay.cpu().numpy())
     s, c, plan = eiger.join_sum(w.build_keys, w.build_pay, w.probe_keys, w.probe_pay, variant="auto")
-    assert plan.variant in ("phj1", "phj2") and plan.narrow == 1
+    assert plan.variant in ("phj1", "phj2") and plan.narrow == 1 and plan.materialize == "gftr"
     assert (s, c) == expect
+    torch.cuda.empty_cache()
+    s1, c1, _ = eiger.join_sum(w.build_keys, w.build_pay, w.probe_keys, w.probe_pay, variant="auto",
+                               materialize="gfur")
+    assert (s1, c1) == expect
+    torch.cuda.empty_cache()
     s2, c2, _ = eiger.join_sum(w.build_keys, w.build_pay, w.probe_keys, w.probe_pay, variant="static")
     assert (s2, c2) == expect
