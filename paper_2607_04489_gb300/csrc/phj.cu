@@ -241,13 +241,15 @@ constexpr int kJoinWarps = kJoinThreads / kWarp;
 // rank within its (row j, warp) group, one scan over the kN x warps group
 // counts places the groups, one global atomic reserves the round's output,
 // and each warp then writes its group to consecutive output positions.
+// Thread t reads back only its own stage entries, so no barrier precedes the
+// ballots: the previous round's closing barrier already orders every read of
+// s_grp before the new counts are written.
 template <int kN, bool PAIRS>
 __device__ __forceinline__ void flush_positional(Stage<kJoinStage>& st, uint32_t* s_grp,
                                                  const JoinOut& out, Ctrl* ctrl) {
     const unsigned lane = lane_id();
     const int w = threadIdx.x / kWarp;
     unsigned ball[kN];
-    __syncthreads();
 #pragma unroll
     for (int j = 0; j < kN; ++j) {
         ball[j] = __ballot_sync(0xffffffffu, st.b[j * kJoinThreads + threadIdx.x] != kHole);
