@@ -847,7 +847,9 @@ def run_star(args):
                        "speedup_of_adaptive": sms / ms},
             "arms": {"auto_plan_gfur": {"ms_per_step": gms, "value": tuples / (gms * 1e-3), "unit": "tuples/s"}},
             "roofline": {"bound": "hbm", "kernel": dom["stage"], "achieved": dom["gbs"], "peak": hbm,
-                         "peak_source": peak_src, "unit": "GB/s", "frac": dom["gbs"] / hbm, "traffic": None,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": dom["gbs"] / hbm,
+                         "traffic": recorded_traffic(dom["stage"], f"star{args.theta:g}"
+                                                     if args.selectivity == 1.0 else None),
                          "algorithmic_bytes": dom["bytes"]},
             "stages": rows, "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
