@@ -203,7 +203,7 @@ eiger_status eiger_join_sum_workspace(int64_t nb, int64_t np, eiger_dtype dtype,
  *          columns (any variant). EIGER_GFTR carries both columns through the
  *          partitioning (PHJ1/PHJ2) or sort (SMJ) passes and reads them by
  *          position, so the probe side's reads are sequential; rejected for
- *          NPHJ/STATIC. EIGER_MAT_AUTO takes GFTR for PHJ and SMJ plans.
+ *          NPHJ/STATIC. EIGER_MAT_AUTO decides as in eiger_join_wide.
  *          plan_used.materialize reports the strategy that ran.
  * Workspace: eiger_join_sum_workspace. Arguments otherwise as eiger_join.
  * out_sum, out_count: host.
@@ -250,7 +250,11 @@ eiger_status eiger_join_wide_workspace(int64_t nb, int64_t np, eiger_dtype dtype
  *          variant). EIGER_GFTR carries the columns through the partitioning
  *          passes (PHJ1/PHJ2) or the sort passes (SMJ) and gathers them from
  *          those copies by position; it is rejected for NPHJ/STATIC.
- *          EIGER_MAT_AUTO takes GFTR for PHJ and SMJ plans and GFUR otherwise.
+ *          EIGER_MAT_AUTO takes GFTR for a PHJ or SMJ plan when carrying
+ *          should move fewer DRAM bytes than gathering (every pass reads and
+ *          writes each carried column, against one 32-byte sector per match
+ *          and column gathered; matches estimated from the build keys'
+ *          distinct count), else GFUR.
  * build, probe: host structs (NULL = no columns); both sides' matched rows
  *          are gathered for every given column.
  * plan_used.materialize reports the strategy that ran.

@@ -1,6 +1,7 @@
 // C ABI of libeiger (declared in include/eiger.h): argument validation,
 // workspace carving, the statistics -> plan -> variant pipeline, and the
 // mapping of CUDA and device-side errors to statuses.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -325,7 +326,8 @@ eiger_status resolve_plan(const JoinCall& c, const eiger_stats_t* bst, eiger_pla
             return fail(EIGER_ERR_INVALID_ARG, "use variant EIGER_STATIC, not a STATIC knob plan");
         pub->selector = 2;
     } else {
-        *pub = plan_rules(c.variant, c.nb, c.np, c.dtype, nok, l2_bytes_or_default());
+        *pub = plan_rules(c.variant, c.nb, c.np, c.dtype, nok, distinct_keys(bst->estimate, c.nb),
+                          l2_bytes_or_default());
     }
     if (c.dtype == EIGER_I32) pub->narrow = 1;  // int32 keys always travel as 32-bit offsets
     eiger_status s = check_plan(*pub, c.nb, c.dtype, nok);
@@ -350,17 +352,38 @@ void sort_passes(eiger_plan_t* p) {
     p->bits1 = sb == 0 ? 1 : (sb + passes - 1) / passes;
 }
 
+// Whether carrying the payload columns through the passes (GFTR) should move
+// fewer DRAM bytes than gathering them by tuple ID (GFUR), the trade-off
+// Sec. 5.2.3 measures as a switch-over by match ratio. Carrying reads and
+// writes every carried column of both sides once per pass; gathering reads,
+// per match and column, at least one 32-byte sector at a random position
+// (columns far larger than L2). Matches are estimated as np times the average
+// build multiplicity nb / distinct build keys (every probe row assumed to
+// match). For |R| = 2^16, |S| = 2^28 and three 4-byte columns per side this
+// puts the switch at a quarter of the probe rows matching.
+bool carry_pays(const JoinCall& c, const eiger_plan_t& p, const eiger_stats_t* bst) {
+    const double passes = p.variant == EIGER_PHJ2 ? 2.0 : p.variant == EIGER_SMJ ? (double)p.bits2 : 1.0;
+    double wb = 0, wp = 0;
+    for (int q = 0; q < c.out.b.n; ++q) wb += c.out.b.bytes[q];
+    for (int q = 0; q < c.out.p.n; ++q) wp += c.out.p.bytes[q];
+    const double carried = 2.0 * passes * ((double)c.nb * wb + (double)c.np * wp);
+    const double distinct = bst && bst->estimate >= 1.0 ? std::min(bst->estimate, (double)c.nb) : (double)c.nb;
+    const double matches = (double)c.np * (double)c.nb / (distinct > 0 ? distinct : 1.0);
+    const double gathered = matches * 32.0 * (double)(c.out.b.n + c.out.p.n);
+    return carried < gathered;
+}
+
 // Materialisation that runs: GFTR needs a transformation (partitioning or
 // sorting) and at least one column to carry (the aggregate carries the two
-// summed payload columns).
-eiger_status resolve_materialize(const JoinCall& c, eiger_plan_t* pub) {
+// summed payload columns); AUTO takes it when carry_pays says so.
+eiger_status resolve_materialize(const JoinCall& c, const eiger_stats_t* bst, eiger_plan_t* pub) {
     const bool transformed = pub->variant == EIGER_PHJ1 || pub->variant == EIGER_PHJ2 || pub->variant == EIGER_SMJ;
     const bool cols = c.out.b.n + c.out.p.n > 0;
     int m = c.materialize;
     if (m == EIGER_GFTR && !transformed)
         return fail(EIGER_ERR_INVALID_ARG, "GFTR needs a partitioned or sort-merge plan (got variant %d)",
                     pub->variant);
-    if (m == EIGER_MAT_AUTO) m = transformed ? EIGER_GFTR : EIGER_GFUR;
+    if (m == EIGER_MAT_AUTO) m = transformed && carry_pays(c, *pub, bst) ? EIGER_GFTR : EIGER_GFUR;
     if (!cols) m = EIGER_GFUR;
     pub->materialize = m;
     return EIGER_OK;
@@ -444,7 +467,7 @@ eiger_status run_join(const JoinCall& c) {
         s = resolve_plan(c, adaptive ? &bst : nullptr, &pub);
         if (s != EIGER_OK) return s;
     }
-    s = resolve_materialize(c, &pub);
+    s = resolve_materialize(c, adaptive ? &bst : nullptr, &pub);
     if (s != EIGER_OK) return s;
     if (c.plan_used) *c.plan_used = pub;
 
@@ -535,9 +558,11 @@ size_t join_workspace_bytes(int64_t nb, int64_t np, int dtype, int variant, cons
     } else {
         const size_t l2 = l2_bytes_or_default();
         for (int nok = 0; nok < 2; ++nok) {
-            eiger_plan_t p = plan_rules(variant, nb, np, dtype, nok != 0, l2);
-            p.narrow = (dtype == EIGER_I32 || nok) ? 1 : 0;
-            consider(p);
+            for (int distinct = 0; distinct < 2; ++distinct) {  // the statistics decide both later
+                eiger_plan_t p = plan_rules(variant, nb, np, dtype, nok != 0, distinct != 0, l2);
+                p.narrow = (dtype == EIGER_I32 || nok) ? 1 : 0;
+                consider(p);
+            }
             if (variant == EIGER_AUTO)  // a learned selector may pick any class
                 for (int cls = 0; cls < EIGER_MLP_OUT; ++cls) {
                     eiger_plan_t q = class_plan(cls);
@@ -621,7 +646,7 @@ eiger_status eiger_plan(const eiger_stats_t* build, const eiger_stats_t* probe, 
     if (nb < 0 || np < 0 || nb > kMaxRows || np > kMaxRows)
         return fail(EIGER_ERR_INVALID_ARG, "row counts must be in [0, 2^32)");
     const bool nok = narrowable(dtype, nb, build->min, build->max);
-    *out = plan_rules(EIGER_AUTO, nb, np, dtype, nok, l2_bytes_or_default());
+    *out = plan_rules(EIGER_AUTO, nb, np, dtype, nok, distinct_keys(build->estimate, nb), l2_bytes_or_default());
     if (dtype == EIGER_I32) out->narrow = 1;
     out->key_min = build->min;
     out->key_max = build->max;

@@ -11,8 +11,13 @@
 //    tuples;
 //  - NPHJ while its table (load factor 0.5) fits half of the L2 cache;
 //  - otherwise PHJ with enough radix bits that an average build partition
-//    holds about half a shared-memory table (kTargetRows), in one pass up to
-//    kOnePassBits bits and in two balanced passes beyond.
+//    holds at most half a shared-memory table (kTargetRows), or three
+//    quarters of one when the HyperLogLog estimate says the build keys are
+//    all distinct (kTargetRowsDistinct), in one pass up to kOnePassBits bits
+//    and in two balanced passes beyond. Measured on GB300: with unique build
+//    keys, partitions of 2300-3000 rows beat 1100-1500 rows by 2-16 % (pairs
+//    and the fused sum alike, 4.7M to 150M build rows); with duplicate build
+//    keys the smaller partitions win by 11-16 % (3000 timed joins).
 #include <algorithm>
 #include <cmath>
 
@@ -23,12 +28,19 @@ namespace eiger {
 
 namespace {
 constexpr int64_t kTargetRows = EIGER_BUILD_CAP / 2;  // average build rows per partition
+constexpr int64_t kTargetRowsDistinct = 3 * EIGER_BUILD_CAP / 4;  // ... when the build keys are distinct
+constexpr double kDistinctFraction = 0.9;  // estimate / rows above which the keys count as distinct
 constexpr int kOnePassBits = 8;
 constexpr int kMaxTotalBits = 20;
 }  // namespace
 
-int phj_total_bits(int64_t nb) {
-    const int64_t parts = (nb + kTargetRows - 1) / kTargetRows;
+bool distinct_keys(double estimate, int64_t nb) {
+    return nb > 0 && estimate >= kDistinctFraction * (double)nb;
+}
+
+int phj_total_bits(int64_t nb, bool distinct) {
+    const int64_t target = distinct ? kTargetRowsDistinct : kTargetRows;
+    const int64_t parts = (nb + target - 1) / target;
     int b = 0;
     while ((1ll << b) < parts) ++b;
     if (b < 2) b = 2;
@@ -43,7 +55,7 @@ unsigned long long table_slots(int64_t nb, double load_factor) {
     return s;
 }
 
-eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool narrowable,
+eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool narrowable, bool distinct,
                         size_t l2_bytes) {
     (void)np;
     eiger_plan_t p{};
@@ -51,7 +63,7 @@ eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool nar
     p.load_factor = 0.5f;
     p.narrow = narrowable ? 1 : 0;
     const bool key32 = dtype == EIGER_I32 || narrowable;
-    const int B = phj_total_bits(nb);
+    const int B = phj_total_bits(nb, distinct);
     int v = variant;
     if (v == EIGER_AUTO) {
         const unsigned long long bytes = table_slots(nb, 0.5) * (key32 ? 8ull : 16ull);

@@ -8,15 +8,19 @@
 
 namespace eiger {
 
-// Radix bits the partitioned join uses for nb build rows.
-int phj_total_bits(int64_t nb);
+// Whether a HyperLogLog estimate says nb build keys are (nearly) all distinct.
+bool distinct_keys(double estimate, int64_t nb);
+
+// Radix bits the partitioned join uses for nb build rows (distinct: the build
+// keys are all distinct, which allows larger partitions).
+int phj_total_bits(int64_t nb, bool distinct);
 
 // Power-of-two slot count of a hash table holding nb rows at load_factor.
 unsigned long long table_slots(int64_t nb, double load_factor);
 
-// Plan for `variant` (EIGER_AUTO lets the rules choose) from sizes and
-// whether the build keys narrow to 32 bits.
-eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool narrowable,
+// Plan for `variant` (EIGER_AUTO lets the rules choose) from sizes, whether
+// the build keys narrow to 32 bits and whether they are distinct.
+eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool narrowable, bool distinct,
                         size_t l2_bytes);
 
 // HyperLogLog estimate from 2^14 dense registers (Sec. 4.1).

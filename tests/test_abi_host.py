@@ -67,6 +67,21 @@ def test_planner_large_build_partitions_in_two_passes(lib):
     assert p.bits1 + p.bits2 == 15 and abs(p.bits1 - p.bits2) <= 1
 
 
+def test_planner_distinct_build_keys_get_larger_partitions(lib):
+    """All-distinct build keys (HyperLogLog estimate >= 0.9 x rows) aim at up
+    to 3072 rows per partition, duplicate-heavy ones at up to 2048."""
+    nb = 150_000_000
+    uniq = lib.plan(_stats(nb, 1, nb), None, nb, 4 * nb, lib.I32)
+    dups = lib.plan(_stats(nb, 1, nb, est=nb / 10), None, nb, 4 * nb, lib.I32)
+    assert (uniq.bits1, uniq.bits2) == (8, 8) and (dups.bits1, dups.bits2) == (9, 8)
+    # 2^26 rows: 4096-row partitions would spill past one table, so both stay at 15 bits
+    for est in (1 << 26, 1 << 22):
+        p = lib.plan(_stats(1 << 26, 0, (1 << 26) - 1, est=est), None, 1 << 26, 1 << 28, lib.I64)
+        assert p.bits1 + p.bits2 == 15
+    assert lib.plan(_stats(1 << 20, 0, 1 << 30, est=0.89 * (1 << 20)), None, 1 << 20, 1 << 22,
+                    lib.I64).variant == "nphj"
+
+
 def test_planner_narrows_only_spans_below_2_32(lib):
     ok = lib.plan(_stats(1 << 24, 10, 10 + 0xFFFFFFFF), None, 1 << 24, 1 << 24, lib.I64)
     wide = lib.plan(_stats(1 << 24, 10, 10 + 0x100000000), None, 1 << 24, 1 << 24, lib.I64)

@@ -249,8 +249,29 @@ def test_join_sum_parity(eiger, oracle_mod, variant, kn, mat):
                                   torch.from_numpy(fk).cuda(), torch.from_numpy(fp).cuda(),
                                   variant=variant, knobs=knobs, materialize=mat)
     assert (gs, gc) == (s, c)
-    carried = mat == "auto" and plan.variant in ("phj1", "phj2", "smj")
-    assert plan.materialize == ("gftr" if carried else "gfur")
+    if mat == "gfur" or plan.variant not in ("phj1", "phj2", "smj"):
+        assert plan.materialize == "gfur"
+
+
+@pytest.mark.parametrize("variant,kn", [("phj2", ("phj2", 4, 4, 1)), ("phj1", ("phj1", 6, 0, 1))])
+def test_join_sum_auto_materialisation_follows_the_match_estimate(eiger, oracle_mod, variant, kn):
+    """AUTO carries the payloads when that moves fewer bytes than gathering
+    them (many matches per build row) and gathers them otherwise: 200K
+    distinct build keys with 20K probe rows gathers, with 800K probe rows
+    carries. Both sums stay exact."""
+    rng = np.random.default_rng(33)
+    nb = 200_000
+    bk = (rng.permutation(nb) * 3 + 11).astype(np.int32)
+    bp = rng.integers(-2**40, 2**40, size=nb).astype(np.int64)
+    for npr, want in ((20_000, "gfur"), (800_000, "gftr")):
+        pk = bk[rng.integers(0, nb, size=npr)]
+        pp = rng.integers(-2**40, 2**40, size=npr).astype(np.int64)
+        s, c = oracle_mod.join_sum(bk, bp, pk, pp)
+        gs, gc, plan = eiger.join_sum(torch.from_numpy(bk).cuda(), torch.from_numpy(bp).cuda(),
+                                      torch.from_numpy(pk).cuda(), torch.from_numpy(pp).cuda(),
+                                      variant=variant, knobs=eiger.Plan(*kn))
+        assert (gs, gc) == (s, c)
+        assert plan.materialize == want, (npr, plan)
 
 
 @pytest.mark.parametrize("pay", [np.int32, np.int64])
