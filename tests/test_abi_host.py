@@ -82,6 +82,42 @@ def test_planner_distinct_build_keys_get_larger_partitions(lib):
                     lib.I64).variant == "nphj"
 
 
+def _rules_reference(nb, distinct, key32, l2=126 << 20):
+    """The planning rules restated from their specification (Sec. 5.2.1-5.2.2
+    crossover; partition target 2048 rows, 3072 for distinct build keys):
+    (variant, bits1, bits2)."""
+    slots = 64
+    while slots < nb / 0.5:
+        slots <<= 1
+    if slots * (8 if key32 else 16) <= l2 // 2:
+        return ("nphj", None, None)
+    target = 3072 if distinct else 2048
+    parts = (nb + target - 1) // target
+    b = max(2, min(20, (parts - 1).bit_length()))  # smallest b with 2^b >= parts
+    if b <= 8:
+        return ("phj1", min(b, 12), 0)
+    return ("phj2", (b + 1) // 2, b - (b + 1) // 2)
+
+
+@pytest.mark.parametrize("log2nb", [10, 16, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31])
+@pytest.mark.parametrize("scale", [1.0, 1.12, 1.45, 1.9])
+@pytest.mark.parametrize("distinct", [True, False])
+def test_planner_matches_its_rules_everywhere(lib, log2nb, scale, distinct):
+    """eiger_plan against the rules restated in Python, over build sizes from
+    2^10 to just below 2^32 rows, distinct and duplicate-heavy keys; every PHJ
+    plan keeps the average build partition within one shared-memory table."""
+    nb = min(int((1 << log2nb) * scale), (1 << 32) - 1)
+    est = nb if distinct else nb / 8
+    p = lib.plan(_stats(nb, 0, nb - 1, est=est), None, nb, min(4 * nb, (1 << 32) - 1), lib.I64)
+    want = _rules_reference(nb, distinct, key32=True)
+    got = (p.variant, p.bits1 if p.variant != "nphj" else None, p.bits2 if p.variant != "nphj" else None)
+    assert got == want
+    if p.variant != "nphj":
+        b = p.bits1 + p.bits2
+        assert nb / (1 << b) <= (3072 if distinct else 2048) or b == 20
+        assert b == 2 or nb / (1 << (b - 1)) > (3072 if distinct else 2048)
+
+
 def test_planner_narrows_only_spans_below_2_32(lib):
     ok = lib.plan(_stats(1 << 24, 10, 10 + 0xFFFFFFFF), None, 1 << 24, 1 << 24, lib.I64)
     wide = lib.plan(_stats(1 << 24, 10, 10 + 0x100000000), None, 1 << 24, 1 << 24, lib.I64)
