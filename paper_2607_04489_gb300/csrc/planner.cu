@@ -14,7 +14,8 @@
 //    holds at most half a shared-memory table (kTargetRows), or three
 //    quarters of one when the HyperLogLog estimate says the build keys are
 //    all distinct (kTargetRowsDistinct), in one pass up to kOnePassBits bits
-//    and in two balanced passes beyond. Measured on GB300: with unique build
+//    and in two balanced passes beyond (pass 2 takes an odd count's extra
+//    bit). Measured on GB300: with unique build
 //    keys, partitions of 2300-3000 rows beat 1100-1500 rows by 2-16 % (pairs
 //    and the fused sum alike, 4.7M to 150M build rows); with duplicate build
 //    keys the smaller partitions win by 11-16 % (3000 timed joins).
@@ -77,7 +78,10 @@ eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool nar
         p.bits1 = std::min(B, 12);
         p.bits2 = 0;
     } else if (v == EIGER_PHJ2) {
-        p.bits1 = (B + 1) / 2;
+        // an odd count's extra bit goes to pass 2: measured on GB300, 7 + 8
+        // bits beat 8 + 7 on 2^26 x 2^28 (7.48 against 7.65 ms), while 7 + 9
+        // lost to 8 + 8 on the 150M x 600M sum (22.0 against 20.95 ms)
+        p.bits1 = B / 2;
         p.bits2 = B - p.bits1;
         if (p.bits2 < 1) {
             p.bits1 = 1;

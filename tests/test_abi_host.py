@@ -73,7 +73,7 @@ def test_planner_distinct_build_keys_get_larger_partitions(lib):
     nb = 150_000_000
     uniq = lib.plan(_stats(nb, 1, nb), None, nb, 4 * nb, lib.I32)
     dups = lib.plan(_stats(nb, 1, nb, est=nb / 10), None, nb, 4 * nb, lib.I32)
-    assert (uniq.bits1, uniq.bits2) == (8, 8) and (dups.bits1, dups.bits2) == (9, 8)
+    assert (uniq.bits1, uniq.bits2) == (8, 8) and (dups.bits1, dups.bits2) == (8, 9)
     # 2^26 rows: 4096-row partitions would spill past one table, so both stay at 15 bits
     for est in (1 << 26, 1 << 22):
         p = lib.plan(_stats(1 << 26, 0, (1 << 26) - 1, est=est), None, 1 << 26, 1 << 28, lib.I64)
@@ -96,7 +96,7 @@ def _rules_reference(nb, distinct, key32, l2=126 << 20):
     b = max(2, min(20, (parts - 1).bit_length()))  # smallest b with 2^b >= parts
     if b <= 8:
         return ("phj1", min(b, 12), 0)
-    return ("phj2", (b + 1) // 2, b - (b + 1) // 2)
+    return ("phj2", b // 2, b - b // 2)
 
 
 @pytest.mark.parametrize("log2nb", [10, 16, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31])
