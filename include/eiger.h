@@ -136,7 +136,13 @@ eiger_status eiger_stats(const void* d_keys, int64_t n, eiger_dtype dtype, eiger
  * key distribution decide). Host-only; launches nothing, needs no GPU.
  * build/probe: statistics of the two key columns (probe may be NULL: only its
  *          size np is then used).
- * out:     the chosen plan (variant never EIGER_AUTO; selector = 0).
+ * out:     the chosen plan (variant never EIGER_AUTO; selector = 0): NPHJ
+ *          while its table (load factor 0.5) fits half the L2 cache; else PHJ
+ *          with the fewest radix bits that keep an average build partition at
+ *          or below 2048 rows (3072 when build->estimate >= 0.9 nb, i.e. the
+ *          keys are distinct), in one pass up to 8 bits, else in two passes
+ *          with an odd count's extra bit in the second; narrow = 1 when the
+ *          build range spans < 2^32.
  * Errors: INVALID_ARG.
  */
 eiger_status eiger_plan(const eiger_stats_t* build, const eiger_stats_t* probe, int64_t nb,
