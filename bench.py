@@ -2,23 +2,27 @@
 
 One step = one eiger_join(AUTO) call on resident device inputs: build-side
 statistics (min/max + HyperLogLog++), plan, radix partitioning of both sides,
-the shared-memory join, and the match count readback. The workload is the
-variant-sweep join at nb = 2^26 unique dense int64 build keys (span < 2^32, so
-keys narrow to uint32) and np = 2^28 probe keys drawn uniformly from them;
-output = the 2^28 (build_idx, probe_idx) pairs. Inputs (2.5 GB) exceed the L2
-cache, so no flush is needed between steps.
+the shared-memory join, and the match count readback. The default workload is
+the largest variant-sweep join that fits the 32-bit tuple IDs at ratio 4:
+nb = 2^28 unique dense int64 build keys (span < 2^32, so keys narrow to
+uint32) and np = 2^30 probe keys drawn uniformly from them; output = the 2^30
+(build_idx, probe_idx) pairs. Inputs (10.7 GB) exceed the L2 cache, so no
+flush is needed between steps.
 
-Also measured, on the same inputs: the static hash join (no statistics, no
-narrowing, no partitioning: the single fixed method) and the end-to-end call
-from pinned host buffers (keys copied in, pairs copied out, every step). The
-roofline line takes the dominant stage's algorithmic bytes over its device
-time, both from the library's per-launch CUDA events in the timed region.
+The headline `value` is timed with nothing but the calls between two CUDA
+events. A second pass of the same steps then records per-launch CUDA events
+(eiger_profile) for the stage breakdown and the roofline of the dominant
+kernel. Also measured, on the same inputs: the static hash join (no
+statistics, no narrowing, no partitioning: the single fixed method) and the
+end-to-end call from pinned host buffers (keys copied in, pairs copied out,
+every step).
 
 Multi-GPU: replicas only (each rank joins its own seeded copy; no collective
 on the data path); value = all ranks' tuples / the slowest rank's time.
 
 ``--impl reference`` times the CPU oracle (the unordered_multimap join plus
-canonical sort) on a bounded sample of the same workload.
+canonical sort, probe loop split over the host's cores) on a bounded sample
+of the same workload.
 """
 
 from __future__ import annotations
@@ -47,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["eiger", "reference"], default="eiger")
-    ap.add_argument("--log2-nb", type=int, default=26)
+    ap.add_argument("--log2-nb", type=int, default=28)
     ap.add_argument("--ratio", type=int, default=4)
     ap.add_argument("--keys", choices=["dense", "random"], default="dense")
     ap.add_argument("--theta", type=float, default=0.0)
@@ -65,6 +69,8 @@ def parse():
     ap.add_argument("--log2-rows", type=int, default=28, help="groupby workload: log2 of the rows")
     ap.add_argument("--key-bytes", type=int, choices=[4, 8], default=4, help="wide workload key/payload width")
     ap.add_argument("--batch-joins", type=int, default=4096)
+    ap.add_argument("--profile-steps", type=int, default=3,
+                    help="steps of the separate per-launch profiling pass (stages, roofline)")
     return ap.parse_args()
 
 
@@ -204,9 +210,10 @@ class ClockSampler:
 def sweep_traffic_key(args):
     """Which recorded ncu traffic applies to this run of the sweep workload:
     only the default sizes, keys and skew were captured."""
-    if (args.log2_nb, args.ratio, args.keys, args.theta) != (26, 4, "dense", 0.0):
+    if (args.ratio, args.keys, args.theta) != (4, "dense", 0.0):
         return None
-    return {"auto": "sweep", "smj": "smj"}.get(args.variant)
+    key = {"auto": "sweep", "smj": "smj"}.get(args.variant)
+    return None if key is None else f"{key}{args.log2_nb}"
 
 
 def workload_desc(args):
@@ -216,33 +223,53 @@ def workload_desc(args):
             f"output (build_idx, probe_idx) pairs"), nb, nb * args.ratio
 
 
-def cpu_oracle_sample(args, min_seconds=12.0):
-    """The oracle, as it stands, on a bounded sample of the workload."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def _oracle_leg(bk, pk, threads, min_seconds, max_runs=64):
     import oracle
+
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        if threads == 1:
+            oracle.join(bk, pk)
+        else:
+            oracle.join_mt(bk, pk, threads)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or runs >= max_runs:
+            break
+    return runs * (bk.size + pk.size) / el, runs, el
+
+
+def cpu_oracle_sample(args, min_seconds=10.0):
+    """The oracle, as it stands, on a bounded sample of the workload: once on
+    all host cores (the probe loop split, -t N) and once on one thread."""
     from paper_2607_04489_gb300 import workloads
 
     log2 = min(args.log2_nb, 20)
     w = workloads.variant_sweep(1 << log2, args.ratio, keys=args.keys, theta=args.theta, seed=0,
                                 device="cpu", payload_bytes=8)
     bk, pk = w.build_keys.numpy(), w.probe_keys.numpy()
-    runs, t0 = 0, time.perf_counter()
-    while True:
-        oracle.join(bk, pk)
-        runs += 1
-        el = time.perf_counter() - t0
-        if el >= min_seconds or runs >= 64:
-            break
-    tput = runs * (bk.size + pk.size) / el
-    return {"value": tput, "unit": "tuples/s", "cores": 1, "kind": "oracle",
-            "sample": f"nb=2^{log2}, np={args.ratio}*2^{log2}, same key/probe distribution; "
-                      f"{runs} run(s) of the full join with canonical pair sort in {el:.1f} s"}
+    cores = host_cores()
+    tn, rn, en = _oracle_leg(bk, pk, cores, min_seconds)
+    t1, r1, e1 = _oracle_leg(bk, pk, 1, min_seconds)
+    sample = f"nb=2^{log2}, np={args.ratio}*2^{log2}, same key/probe distribution"
+    return {"value": tn, "unit": "tuples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sample}; {rn} run(s) of the full join with canonical pair sort in {en:.1f} s, "
+                      f"probe loop split over {cores} threads (multimap build and sort on one)",
+            "one_thread": {"value": t1, "unit": "tuples/s", "cores": 1,
+                           "sample": f"{sample}; {r1} run(s) in {e1:.1f} s"}}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import oracle
     from paper_2607_04489_gb300 import workloads
 
     desc, nb, np_ = workload_desc(args)
@@ -250,20 +277,24 @@ def run_reference(args):
     w = workloads.variant_sweep(1 << log2, args.ratio, keys=args.keys, theta=args.theta, seed=0,
                                 device="cpu", payload_bytes=8)
     bk, pk = w.build_keys.numpy(), w.probe_keys.numpy()
+    cores = host_cores()
+    import oracle
+
     for _ in range(args.warmup):
-        oracle.join(bk, pk)
+        oracle.join_mt(bk, pk, cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.join(bk, pk)
+        oracle.join_mt(bk, pk, cores)
     el = time.perf_counter() - t0
     tput = args.steps * (bk.size + pk.size) / el
-    sample = f"nb=2^{log2}, np={args.ratio}*2^{log2} per step (bounded sample of the workload)"
+    sample = (f"nb=2^{log2}, np={args.ratio}*2^{log2} per step (bounded sample of the workload), "
+              f"probe loop split over {cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": tput, "unit": "tuples/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": desc, "nb": nb, "np": np_},
-            "cpu_baseline": {"value": tput, "unit": "tuples/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": tput, "unit": "tuples/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": tput, "unit": "tuples/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -295,6 +326,7 @@ def run_eiger(args):
     ws = torch.empty(eiger.join_workspace(nb, np_, eiger.I64, args.variant), dtype=torch.uint8,
                      device=dev)
     stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def step(variant, workspace):
         st, cnt, plan = eiger.join_into(bk, pk, variant=variant, out_bidx=out_b, out_pidx=out_p,
@@ -303,33 +335,46 @@ def run_eiger(args):
             raise RuntimeError(f"join failed: status {st}, count {cnt}: {eiger.last_error()}")
         return plan
 
-    # ---- adaptive join: warm-up, then the timed region with per-launch events
+    def timed(variant, workspace, steps):
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            plan = step(variant, workspace)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world, dev), plan
+
+    # ---- adaptive join: warm-up, then the timed region (nothing but the calls)
     for _ in range(args.warmup):
         plan = step(args.variant, ws)
-    eiger.profile(True)
+    sampler = ClockSampler(local).start()
+    ms_step, plan = timed(args.variant, ws, args.steps)
+    clocks = sampler.stop()
+    tuples = world * (nb + np_)
+    value = tuples / (ms_step * 1e-3)
+
+    # ---- the same steps again with per-launch CUDA events (stage breakdown)
     stages = {}
     launches = 0
-    sampler = ClockSampler(local).start()
+    eiger.profile(True)
     barrier(world)
     torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        plan = step(args.variant, ws)
+    for _ in range(args.profile_steps):
+        step(args.variant, ws)
         for name, ms, nl, by in eiger.profile_read():
-            s = stages.setdefault(name, [0.0, 0.0, 0])
-            s[0] += ms
-            s[1] += by
-            s[2] += 1
+            s_ = stages.setdefault(name, [0.0, 0.0, 0])
+            s_[0] += ms
+            s_[1] += by
+            s_[2] += 1
             launches += nl
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    barrier(world)
-    clocks = sampler.stop()
     eiger.profile(False)
-    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
-    tuples = world * (nb + np_)
-    value = tuples / (ms_step * 1e-3)
+    ms_prof = e0.elapsed_time(e1) / max(1, args.profile_steps)
+    launches_per_step = launches // max(1, args.profile_steps)
 
     # ---- the static hash join on the same inputs
     static = None
@@ -340,15 +385,7 @@ def run_eiger(args):
                            device=dev)
         for _ in range(args.warmup):
             step("static", ws_s)
-        barrier(world)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step("static", ws_s)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier(world)
-        sms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        sms, _ = timed("static", ws_s, args.steps)
         static = {"value": tuples / (sms * 1e-3), "unit": "tuples/s", "ms_per_step": sms,
                   "speedup_of_adaptive": sms / ms_step}
         del ws_s
@@ -356,17 +393,21 @@ def run_eiger(args):
         ws = torch.empty(eiger.join_workspace(nb, np_, eiger.I64, args.variant), dtype=torch.uint8,
                          device=dev)
 
-    # ---- end to end through the public API from pinned host buffers. Every
-    # step copies its own keys in and its pairs out; consecutive steps are
-    # pipelined over three streams with double-buffered device arrays, as a
-    # caller streaming batches would run them: step i+1's upload and step
-    # i-1's download overlap step i's join.
+    # ---- end to end from pinned host buffers. Every step copies its own keys
+    # in and its pairs out (torch copies on two extra streams around the
+    # device-pointer C-ABI call, eiger_join); consecutive steps are pipelined
+    # with double-buffered device arrays, as a caller streaming batches would
+    # run them: step i+1's upload and step i-1's download overlap step i's
+    # join. The downloads of all steps land in one pinned host pair (copies on
+    # one stream run in order).
     e2e = None
     if not args.no_e2e:
-        hb = bk.cpu().pin_memory()
-        hp = pk.cpu().pin_memory()
-        hob = [torch.empty(np_, dtype=torch.int32).pin_memory() for _ in range(2)]
-        hop = [torch.empty(np_, dtype=torch.int32).pin_memory() for _ in range(2)]
+        hb = torch.empty(nb, dtype=bk.dtype, pin_memory=True)
+        hp = torch.empty(np_, dtype=pk.dtype, pin_memory=True)
+        hb.copy_(bk)
+        hp.copy_(pk)
+        hob = torch.empty(np_, dtype=torch.int32, pin_memory=True)
+        hop = torch.empty(np_, dtype=torch.int32, pin_memory=True)
         dbk = [bk, torch.empty_like(bk)]
         dpk = [pk, torch.empty_like(pk)]
         dob = [out_b, torch.empty_like(out_b)]
@@ -401,8 +442,8 @@ def run_eiger(args):
                 join_done[slot].record(stream)
                 d2h.wait_event(join_done[slot])
                 with torch.cuda.stream(d2h):
-                    hob[slot].copy_(dob[slot], non_blocking=True)
-                    hop[slot].copy_(dop[slot], non_blocking=True)
+                    hob.copy_(dob[slot], non_blocking=True)
+                    hop.copy_(dop[slot], non_blocking=True)
                 down_done[slot].record(d2h)
 
         run_steps(max(2, args.warmup))
@@ -422,19 +463,15 @@ def run_eiger(args):
         e2e = {"value": tuples / (ems * 1e-3), "unit": "tuples/s", "ms_per_step": ems,
                "h2d_bytes_per_step": int(bk.numel() * 8 + pk.numel() * 8),
                "d2h_bytes_per_step": int(2 * 4 * np_),
+               "through": "torch copies from/to pinned host memory around the device-pointer C-ABI call "
+                          "eiger_join (the ABI takes device pointers)",
                "pipelining": "upload of step i+1 and download of step i-1 overlap the join of step i"}
-        del dbk[1], dpk[1], dob[1], dop[1]
+        del dbk[1], dpk[1], dob[1], dop[1], hb, hp, hob, hop
 
-    # ---- roofline of the dominant stage
+    # ---- roofline of the dominant stage (from the profiling pass)
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    stage_rows = []
-    for name, (ms_tot, by_tot, cnt) in stages.items():
-        ms_avg = ms_tot / cnt
-        by_avg = by_tot / cnt
-        stage_rows.append({"stage": name, "ms": round(ms_avg, 4), "bytes": by_avg,
-                           "gbs": by_avg / (ms_avg * 1e-3) / 1e9 if ms_avg > 0 else None})
-    stage_rows.sort(key=lambda r: -r["ms"])
+    stage_rows = stage_table(stages)
     dom = stage_rows[0]
     compulsory = nb * 8 + np_ * 8 + np_ * 8  # keys in, pairs out
     line = {
@@ -443,7 +480,8 @@ def run_eiger(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
         "config": {"workload": desc, "nb": nb, "np": np_, "keys": args.keys, "theta": args.theta,
-                   "variant": args.variant, "l2": "inputs (2.5 GB) larger than L2; no flush",
+                   "variant": args.variant,
+                   "l2": f"inputs ({(nb + np_) * 8 / 1e9:.1f} GB) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "hbm_gbs_compulsory": compulsory / (ms_step * 1e-3) / 1e9,
         "plan": {"variant": plan.variant, "bits1": plan.bits1, "bits2": plan.bits2,
@@ -451,9 +489,12 @@ def run_eiger(args):
         "roofline": {"bound": "hbm", "kernel": dom["stage"], "achieved": dom["gbs"], "peak": hbm,
                      "peak_source": peak_src, "unit": "GB/s", "frac": dom["gbs"] / hbm,
                      "traffic": recorded_traffic(dom["stage"], sweep_traffic_key(args)),
-                     "algorithmic_bytes": dom["bytes"]},
+                     "algorithmic_bytes": dom["bytes"],
+                     "timing": f"CUDA events around each launch on its stream, {args.profile_steps} "
+                               "profiled steps after the timed region"},
         "stages": stage_rows,
-        "gpu_launches": launches,
+        "profiled_ms_per_step": ms_prof,
+        "gpu_launches": launches_per_step * args.steps,
         "static": static,
         "e2e": e2e,
         "clocks": clocks,

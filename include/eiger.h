@@ -479,7 +479,8 @@ eiger_status eiger_selector_set(const float* d_params, const float* h_feature_me
  * larger ones return EIGER_ERR_INVALID_ARG before any GPU work.
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before any stream
- * capture begins. All calls on a device share the array and each clears it on
+ * capture begins. Call it under the device's primary context (the CUDA
+ * runtime's). All calls on a device share the array and each clears it on
  * its stream first, so consecutive calls are independent, but calls whose
  * work overlaps on the GPU (other streams, other threads) race on it.
  * Synchronises `stream`. Errors: INVALID_ARG, CAPACITY, TABLE_FULL, CUDA,

@@ -38,6 +38,12 @@ def _load():
     lib.oracle_join.restype = c.c_int64
     lib.oracle_join.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_void_p, c.c_int64,
                                 c.c_void_p, c.c_void_p, c.c_int64]
+    lib.oracle_join_mt.restype = c.c_int64
+    lib.oracle_join_mt.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_void_p, c.c_int64,
+                                   c.c_void_p, c.c_void_p, c.c_int64, c.c_int]
+    lib.oracle_join_fingerprint.restype = c.c_int64
+    lib.oracle_join_fingerprint.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_void_p, c.c_int64, c.c_int,
+                                            c.POINTER(c.c_uint64), c.POINTER(c.c_uint64)]
     lib.oracle_join_count.restype = c.c_int64
     lib.oracle_join_count.argtypes = [c.c_int, c.c_void_p, c.c_int64, c.c_void_p, c.c_int64]
     lib.oracle_join_sum.restype = c.c_int64
@@ -92,6 +98,38 @@ def join(build_keys, probe_keys, cap=None):
     n = lib.oracle_join(dt, _ptr(bk), bk.size, _ptr(pk), pk.size, _ptr(out_b), _ptr(out_p), cap)
     k = min(n, cap)
     return out_b[:k].copy(), out_p[:k].copy(), int(n)
+
+
+def join_mt(build_keys, probe_keys, threads: int):
+    """``join`` with the probe loop split over ``threads`` host threads (the
+    oracle's -t N mode); the output is identical to ``join``'s."""
+    bk, dt = _keys(build_keys)
+    pk, dt2 = _keys(probe_keys)
+    if dt != dt2:
+        raise TypeError("build and probe keys must share a dtype")
+    lib = _load()
+    cap = lib.oracle_join_count(dt, _ptr(bk), bk.size, _ptr(pk), pk.size)
+    out_b = np.empty(max(cap, 1), np.uint32)
+    out_p = np.empty(max(cap, 1), np.uint32)
+    n = lib.oracle_join_mt(dt, _ptr(bk), bk.size, _ptr(pk), pk.size, _ptr(out_b), _ptr(out_p), cap,
+                           int(threads))
+    return out_b[:n].copy(), out_p[:n].copy(), int(n)
+
+
+def join_fingerprint(build_keys, probe_keys, threads: int = 1):
+    """(|J|, fp_sum, fp_xor) of the join's pair multiset without storing it:
+    with w = build_idx * 2^32 + probe_idx per pair, fp_sum = sum of h64(w)
+    mod 2^64 and fp_xor = xor of h64(w + 0x9E3779B97F4A7C15), both as Python
+    ints in [0, 2^64). For results too large to sort on the host."""
+    bk, dt = _keys(build_keys)
+    pk, dt2 = _keys(probe_keys)
+    if dt != dt2:
+        raise TypeError("build and probe keys must share a dtype")
+    s = ctypes.c_uint64(0)
+    x = ctypes.c_uint64(0)
+    n = _load().oracle_join_fingerprint(dt, _ptr(bk), bk.size, _ptr(pk), pk.size, int(threads),
+                                        ctypes.byref(s), ctypes.byref(x))
+    return int(n), int(s.value), int(x.value)
 
 
 def join_wide(build_keys, probe_keys, build_cols=(), probe_cols=()):

@@ -22,7 +22,7 @@ def build_oracle(verbose: bool = False) -> str:
     src = os.path.join(HERE, "oracle.cpp")
     out = library_path()
     tmp = out + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", src, "-o", tmp]
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-pthread", "-shared", "-fPIC", src, "-o", tmp]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

@@ -6,11 +6,15 @@
 // leg of the benchmark load it. It shares no code, header, table or constant
 // generator with the CUDA path. Every function is the plain definition of what
 // the GPU path computes, written for a reader who checks it against the paper:
-// no blocking, no fusion, single-threaded, fp64 where floating point occurs.
+// no blocking, no fusion, fp64 where floating point occurs. Single-threaded,
+// except the "-t N" entry points (oracle_join_mt, oracle_join_fingerprint),
+// which split only the probe loop over host threads.
 //
 // Pins (checked by the CPU tests, independent of this file):
 //   join            nested-loop brute force; |J| = sum_k cnt_R(k) * cnt_S(k);
 //                   closed forms of the permutation workloads.
+//   join (-t N)     identical output to the one-thread join.
+//   fingerprint     the sum / xor of h64 over brute-force pairs, in Python.
 //   join sum        direct addressing over dense dimension keys.
 //   h64             published SplitMix64 output sequence; bijectivity.
 //   hll registers   multiset/set invariance, union = register-wise max.
@@ -21,7 +25,7 @@
 //   group-by        Python dict brute force; sum of counts = rows; sum of
 //                   group sums = column sum; closed forms of i mod g keys.
 //
-// Build: g++ -O2 -std=c++17 -ffp-contract=off -shared -fPIC oracle.cpp
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -pthread -shared -fPIC oracle.cpp
 // (-ffp-contract=off keeps the estimate formula evaluated exactly as written.)
 
 #include <algorithm>
@@ -29,6 +33,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <unordered_map>
 #include <utility>
 #include <vector>
@@ -107,6 +112,103 @@ int64_t oracle_join(int dtype, const void* bkeys, int64_t nb, const void* pkeys,
         out_b[k] = pairs[k].second;
     }
     return count;
+}
+
+// The same join with the probe loop split over `threads` host threads (the
+// oracle's "-t N" mode, for timing on a many-core host). The multimap is built
+// by one thread as above; thread t probes the contiguous probe rows
+// [t*np/threads, (t+1)*np/threads) in order and keeps its pairs; the lists are
+// concatenated in thread order and sorted canonically, so the output is
+// identical to oracle_join's. Returns |J|; writes at most `cap` pairs.
+int64_t oracle_join_mt(int dtype, const void* bkeys, int64_t nb, const void* pkeys, int64_t np,
+                       uint32_t* out_b, uint32_t* out_p, int64_t cap, int threads) {
+    if (threads < 1) threads = 1;
+    std::unordered_multimap<int64_t, uint32_t> table;
+    table.reserve((size_t)nb);
+    for (int64_t i = 0; i < nb; ++i) table.emplace(key_at(dtype, bkeys, i), (uint32_t)i);
+
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> part((size_t)threads);
+    auto probe_range = [&](int t) {
+        const int64_t lo = np * t / threads, hi = np * (t + 1) / threads;
+        for (int64_t j = lo; j < hi; ++j) {
+            auto range = table.equal_range(key_at(dtype, pkeys, j));
+            for (auto it = range.first; it != range.second; ++it) {
+                part[(size_t)t].emplace_back((uint32_t)j, it->second);
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(probe_range, t);
+    probe_range(0);
+    for (auto& th : pool) th.join();
+
+    std::vector<std::pair<uint32_t, uint32_t>> pairs;  // (probe, build)
+    int64_t count = 0;
+    for (int t = 0; t < threads; ++t) {
+        for (const auto& pr : part[(size_t)t]) {
+            if (count < cap) pairs.push_back(pr);
+            ++count;
+        }
+        std::vector<std::pair<uint32_t, uint32_t>>().swap(part[(size_t)t]);
+    }
+    std::sort(pairs.begin(), pairs.end());
+    for (size_t k = 0; k < pairs.size(); ++k) {
+        out_p[k] = pairs[k].first;
+        out_b[k] = pairs[k].second;
+    }
+    return count;
+}
+
+// Order-independent summary of a join result too large to sort on the host:
+// |J| and two 64-bit fingerprints of the pair multiset, with the pair (i, j)
+// read as the 64-bit word w = i * 2^32 + j:
+//   fp_sum = sum over J of h64(w)              (mod 2^64)
+//   fp_xor = xor over J of h64(w + 0x9E3779B97F4A7C15)
+// (the second is h64 at SplitMix64's next state, a different mixing of the
+// same word). Equal multisets give equal summaries; a missing, extra or
+// altered pair changes both fingerprints except with probability ~2^-64. The
+// pairs are produced by the same multimap definition as oracle_join and
+// streamed, never stored; the probe loop is split over `threads` host threads
+// (modular sums and xors of the per-thread parts do not depend on the split).
+int64_t oracle_join_fingerprint(int dtype, const void* bkeys, int64_t nb, const void* pkeys, int64_t np,
+                                int threads, uint64_t* fp_sum, uint64_t* fp_xor) {
+    if (threads < 1) threads = 1;
+    std::unordered_multimap<int64_t, uint32_t> table;
+    table.reserve((size_t)nb);
+    for (int64_t i = 0; i < nb; ++i) table.emplace(key_at(dtype, bkeys, i), (uint32_t)i);
+    std::vector<uint64_t> s((size_t)threads, 0), x((size_t)threads, 0);
+    std::vector<int64_t> c((size_t)threads, 0);
+    auto probe_range = [&](int t) {
+        const int64_t lo = np * t / threads, hi = np * (t + 1) / threads;
+        uint64_t ss = 0, xx = 0;
+        int64_t cc = 0;
+        for (int64_t j = lo; j < hi; ++j) {
+            auto range = table.equal_range(key_at(dtype, pkeys, j));
+            for (auto it = range.first; it != range.second; ++it) {
+                const uint64_t w = ((uint64_t)it->second << 32) | (uint64_t)(uint32_t)j;
+                ss += h64(w);
+                xx ^= h64(w + 0x9E3779B97F4A7C15ULL);
+                ++cc;
+            }
+        }
+        s[(size_t)t] = ss;
+        x[(size_t)t] = xx;
+        c[(size_t)t] = cc;
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(probe_range, t);
+    probe_range(0);
+    for (auto& th : pool) th.join();
+    uint64_t ss = 0, xx = 0;
+    int64_t cc = 0;
+    for (int t = 0; t < threads; ++t) {
+        ss += s[(size_t)t];
+        xx ^= x[(size_t)t];
+        cc += c[(size_t)t];
+    }
+    *fp_sum = ss;
+    *fp_xor = xx;
+    return cc;
 }
 
 // |J| only, with no pair storage (same multimap definition as above).

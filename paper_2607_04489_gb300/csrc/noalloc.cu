@@ -22,8 +22,11 @@
 //    (different streams, or different host threads) race on the array.
 //  - The host needs the array's device address, which is not the address of
 //    the symbol in host code. The first call on each device looks it up with
-//    cudaGetSymbolAddress (that device current) and caches it; make that first
-//    call before any stream capture begins.
+//    cudaGetSymbolAddress (that device current) and caches it per device
+//    ordinal; make that first call before any stream capture begins. The
+//    cached address belongs to the device's primary context (the one the CUDA
+//    runtime uses): call this entry point under that context, not under a
+//    context pushed through the driver API.
 #include <mutex>
 
 #include "eiger.h"
@@ -41,6 +44,11 @@ constexpr size_t kCtrlBytes = 256;
 constexpr size_t kTableBytes = (size_t)8 << 20;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kCtrlBytes + kTableBytes];
+
+// The control block sits in the first kCtrlBytes; the table starts right
+// after it, on a 256-byte boundary.
+static_assert(sizeof(Ctrl) <= kCtrlBytes, "control block overflows its slot of the scratch array");
+static_assert(kCtrlBytes % 256 == 0, "table offset must keep 256-byte alignment");
 
 std::mutex g_addr_mu;
 void* g_addr[64];

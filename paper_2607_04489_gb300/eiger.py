@@ -634,9 +634,30 @@ def join_static_noalloc_into(build_keys, probe_keys, out_bidx, out_pidx, capacit
                              stream=None):
     """eiger_join_static_noalloc into caller-owned outputs: the static join
     with its scratch in the library's fixed device array (for callers that
-    cannot allocate). Returns (status, count)."""
-    lib = load()
+    cannot allocate). Returns (status, count).
+
+    The kernels read and write through raw pointers, so every argument is
+    checked here first, as join() does: both key columns contiguous CUDA
+    tensors of one dtype (int32 or int64); each output None or a contiguous
+    int32 CUDA tensor of at least `capacity` entries."""
+    if capacity < 0:
+        raise ValueError("capacity must be >= 0")
+    for name, t in (("build_keys", build_keys), ("probe_keys", probe_keys)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    if build_keys.dtype != probe_keys.dtype:
+        raise TypeError("build and probe keys must share a dtype")
     dt = _dtype_code(build_keys)
+    if capacity > 0 and out_bidx is None and out_pidx is None:
+        raise ValueError("capacity > 0 needs at least one output tensor")
+    for name, t in (("out_bidx", out_bidx), ("out_pidx", out_pidx)):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or t.dtype != torch.int32:
+            raise TypeError(f"{name} must be a contiguous int32 CUDA tensor")
+        if t.numel() < capacity:
+            raise ValueError(f"{name} holds {t.numel()} entries < capacity {capacity}")
+    lib = load()
     cnt = ctypes.c_int64(0)
     st = lib.eiger_join_static_noalloc(dt, _ptr(build_keys), build_keys.numel(), _ptr(probe_keys),
                                        probe_keys.numel(), _ptr(out_bidx), _ptr(out_pidx), capacity,

@@ -80,6 +80,59 @@ def test_join_matches_nested_loop(oracle_mod, dtype):
         np.testing.assert_array_equal(p, ep)
 
 
+@pytest.mark.parametrize("threads", [1, 2, 3, 8])
+def test_threaded_join_equals_one_thread_and_nested_loop(oracle_mod, threads):
+    """The -t N mode splits only the probe loop: its canonical output is the
+    one-thread join's, element for element, and the brute force's."""
+    rng = np.random.default_rng(31 + threads)
+    for trial in range(12):
+        nb = int(rng.integers(0, 400))
+        np_ = int(rng.integers(0, 700))
+        bk = rng.integers(-20, 20, size=nb).astype(np.int64)
+        pk = rng.integers(-25, 25, size=np_).astype(np.int64)
+        b1, p1, n1 = oracle_mod.join(bk, pk)
+        bt, pt, nt = oracle_mod.join_mt(bk, pk, threads)
+        eb, ep = _nested_loop(bk, pk)
+        assert n1 == nt == eb.size
+        np.testing.assert_array_equal(bt, b1)
+        np.testing.assert_array_equal(pt, p1)
+        np.testing.assert_array_equal(bt, eb)
+        np.testing.assert_array_equal(pt, ep)
+
+
+def _py_h64(z):
+    """SplitMix64's output function in plain Python integers (the published
+    definition; the oracle's h64 is pinned to its sequence above)."""
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+@pytest.mark.parametrize("threads", [1, 4])
+def test_join_fingerprint_matches_brute_force_pairs(oracle_mod, threads):
+    """The streamed fingerprint equals the sum / xor over the nested-loop
+    pairs, with each pair read as build_idx * 2^32 + probe_idx; a swapped
+    side or a dropped pair changes it."""
+    rng = np.random.default_rng(41)
+    bk = rng.integers(0, 30, size=150).astype(np.int32)
+    pk = rng.integers(0, 40, size=260).astype(np.int32)
+    eb, ep = _nested_loop(bk, pk)
+    s = x = 0
+    for b, p in zip(eb.tolist(), ep.tolist()):
+        w = (b << 32) | p
+        s = (s + _py_h64(w)) & M64
+        x ^= _py_h64((w + 0x9E3779B97F4A7C15) & M64)
+    n, fs, fx = oracle_mod.join_fingerprint(bk, pk, threads)
+    assert (n, fs, fx) == (eb.size, s, x)
+    swapped = 0
+    for b, p in zip(eb.tolist(), ep.tolist()):
+        swapped = (swapped + _py_h64((p << 32) | b)) & M64
+    assert swapped != fs
+    assert oracle_mod.join_fingerprint(bk, pk[:-1], threads)[1:] != (fs, fx) or \
+        int((bk == pk[-1]).sum()) == 0
+    assert oracle_mod.join_fingerprint(bk[:0], pk, threads) == (0, 0, 0)
+
+
 def test_join_int64_extremes_and_wide_span(oracle_mod):
     # keys that agree in the low 32 bits but differ above must not match
     bk = np.array([2**32, 0, -2**63, 2**63 - 1, 5, 5], np.int64)
@@ -288,3 +341,24 @@ def test_wide_join_matches_nested_loop_with_columns(oracle_mod):
     got = [(int(p[k]), int(b[k]), tuple(int(c[k]) for c in obc), tuple(int(c[k]) for c in opc))
            for k in range(len(b))]
     assert got == want
+
+
+def test_torch_pair_fingerprint_matches_oracle(oracle_mod):
+    """The torch fingerprint that the full-size GPU tests compute from the
+    GPU's pairs is the oracle's join_fingerprint (on the CPU, from the
+    oracle's own canonical pairs, duplicates and both dtypes)."""
+    import torch
+
+    from fingerprint import pair_fingerprint
+
+    rng = np.random.default_rng(43)
+    for dtype in (np.int32, np.int64):
+        bk = rng.integers(-50, 50, size=3000).astype(dtype)
+        pk = rng.integers(-60, 60, size=7001).astype(dtype)
+        b, p, n = oracle_mod.join(bk, pk)
+        got = pair_fingerprint(torch.from_numpy(b.astype(np.int64)), torch.from_numpy(p.astype(np.int64)),
+                               chunk=4096)
+        assert got == oracle_mod.join_fingerprint(bk, pk, 3)
+        order = rng.permutation(n)  # order-independent
+        assert pair_fingerprint(torch.from_numpy(b[order].astype(np.int64)),
+                                torch.from_numpy(p[order].astype(np.int64))) == got
