@@ -60,11 +60,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-static", action="store_true")
     ap.add_argument("--selectivity", type=float, default=1.0, help="star workload: fact rows kept")
-    ap.add_argument("--workload", choices=["sweep", "batched", "wide", "groupby", "star"], default="sweep",
+    ap.add_argument("--grid-sizes", default="20,22,24,26,28", help="grid workload: log2 build sizes")
+    ap.add_argument("--grid-reps", type=int, default=3, help="grid workload: timed runs per plan")
+    ap.add_argument("--workload", choices=["sweep", "batched", "wide", "groupby", "star", "grid"], default="sweep",
                     help="sweep: the headline join; batched: 4096 small joins in one launch; "
                          "wide: four columns per relation, the payloads materialised; "
                          "groupby: 2^28 rows, two aggregations, 2^--groups-log2 groups; "
-                         "star: the 150M x 600M foreign-key join with the exact payload sum")
+                         "star: the 150M x 600M foreign-key join with the exact payload sum; "
+                         "grid: the variant-sweep grid, every plan timed at every point (one JSON line each)")
     ap.add_argument("--groups-log2", type=int, default=20, help="groupby workload: log2 of the group count")
     ap.add_argument("--log2-rows", type=int, default=28, help="groupby workload: log2 of the rows")
     ap.add_argument("--key-bytes", type=int, choices=[4, 8], default=4, help="wide workload key/payload width")
@@ -472,7 +475,7 @@ def run_eiger(args):
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     stage_rows = stage_table(stages)
-    dom = stage_rows[0]
+    dom = stage_rows[0] if stage_rows else {"stage": None, "gbs": 0.0, "bytes": 0.0}
     compulsory = nb * 8 + np_ * 8 + np_ * 8  # keys in, pairs out
     line = {
         "metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world,
@@ -587,6 +590,107 @@ def stage_table(stages):
                      "gbs": by_avg / (ms_avg * 1e-3) / 1e9 if ms_avg > 0 else None})
     rows.sort(key=lambda r: -r["ms"])
     return rows
+
+
+def grid_plans(nb: int, auto_plan):
+    """Forced plans timed at one variant-sweep point besides AUTO and STATIC:
+    the non-partitioned join, one pass of 6, 8, 10 and 12 radix bits, and two
+    passes of the AUTO plan's total bits and one bit fewer or more (split as
+    the rules split them). Plans whose average build partition would exceed
+    four shared-memory tables (each further table re-streams the probe
+    partition) are listed with a reason instead of being timed."""
+    from paper_2607_04489_gb300 import eiger
+
+    limit = 4 * 4096
+    out = [("nphj", eiger.Plan("nphj", narrow=auto_plan.narrow))]
+    for b in (6, 8, 10, 12):
+        out.append((f"phj1-{b}", eiger.Plan("phj1", b, 0, auto_plan.narrow) if nb >> b <= limit else None))
+    tot = auto_plan.bits1 + auto_plan.bits2 if auto_plan.variant == "phj2" else \
+        auto_plan.bits1 if auto_plan.variant == "phj1" else max(2, (nb // 2048).bit_length())
+    for t in (tot - 1, tot, tot + 1):
+        if 2 <= t <= 24:
+            b1 = t // 2
+            plan = eiger.Plan("phj2", b1, t - b1, auto_plan.narrow)
+            out.append((f"phj2-{b1}+{t - b1}", plan if nb >> t <= limit else None))
+    return out
+
+
+def run_grid(args):
+    """The variant-sweep grid: build sizes 2^k (--grid-sizes), probe ratio 1,
+    4 and 16, dense (narrowable) and random 64-bit keys, probe skew theta 0,
+    0.5, 1 and 1.5. At every point AUTO (statistics and plan included), the
+    static join and the forced plans of grid_plans are each timed
+    --grid-reps times after one warm-up call (the minimum is reported, as the
+    paper reports minima); AUTO's regret is its time over the fastest plan's.
+    Points whose probe side needs 32-bit tuple IDs beyond 2^32 - 1 rows are
+    skipped. One JSON line per point."""
+    import torch
+
+    from paper_2607_04489_gb300 import eiger, workloads
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    eiger.load()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for log2 in [int(x) for x in args.grid_sizes.split(",")]:
+        for ratio in (1, 4, 16):
+            nb = 1 << log2
+            np_ = nb * ratio
+            if np_ >= (1 << 32):
+                continue
+            for keys in ("dense", "random"):
+                for theta in (0.0, 0.5, 1.0, 1.5):
+                    w = workloads.variant_sweep(nb, ratio, keys=keys, theta=theta, seed=0, device=dev,
+                                                payload_bytes=8)
+                    w.build_pay = w.probe_pay = None
+                    torch.cuda.empty_cache()
+                    bk, pk = w.build_keys, w.probe_keys
+                    ob = torch.empty(np_, dtype=torch.int32, device=dev)
+                    op = torch.empty(np_, dtype=torch.int32, device=dev)
+
+                    def timed(variant, knobs):
+                        ws = torch.empty(eiger.join_workspace(nb, np_, eiger.I64, variant, knobs),
+                                         dtype=torch.uint8, device=dev)
+                        best, plan = float("inf"), None
+                        for rep in range(args.grid_reps + 1):
+                            e0.record(stream)
+                            st, cnt, plan = eiger.join_into(bk, pk, variant=variant, knobs=knobs, out_bidx=ob,
+                                                            out_pidx=op, capacity=np_, workspace=ws,
+                                                            stream=stream)
+                            e1.record(stream)
+                            torch.cuda.synchronize(dev)
+                            if st != eiger.OK or cnt != np_:
+                                raise RuntimeError(f"{variant} {knobs}: status {st}, count {cnt}: "
+                                                   f"{eiger.last_error()}")
+                            if rep:
+                                best = min(best, e0.elapsed_time(e1))
+                        del ws
+                        return best, plan
+
+                    auto_ms, auto_plan = timed("auto", None)
+                    static_ms, _ = timed("static", None)
+                    times = {"auto": auto_ms, "static": static_ms}
+                    skipped = []
+                    for name, knobs in grid_plans(nb, auto_plan):
+                        if knobs is None:
+                            skipped.append(name)
+                            continue
+                        times[name], _ = timed(knobs.variant, knobs)
+                    forced = {k: v for k, v in times.items() if k not in ("auto",)}
+                    best_name = min(forced, key=forced.get)
+                    print(json.dumps({
+                        "nb": nb, "np": np_, "keys": keys, "theta": theta,
+                        "auto_plan": f"{auto_plan.variant} {auto_plan.bits1}+{auto_plan.bits2} "
+                                     f"narrow={auto_plan.narrow}",
+                        "ms": {k: round(v, 4) for k, v in times.items()},
+                        "best": best_name, "auto_regret": round(auto_ms / forced[best_name] - 1.0, 4),
+                        "auto_vs_static": round(static_ms / auto_ms, 3),
+                        "auto_tuples_per_s": (nb + np_) / (auto_ms * 1e-3),
+                        "skipped": skipped}), flush=True)
+                    del w, bk, pk, ob, op
+                    torch.cuda.empty_cache()
+    return 0
 
 
 def run_wide(args):
@@ -910,6 +1014,8 @@ def main():
         return run_groupby(args)
     if args.workload == "star":
         return run_star(args)
+    if args.workload == "grid":
+        return run_grid(args)
     return run_eiger(args)
 
 

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeiger.so")
-SOURCES = ["abi.cu", "planner.cu", "profile.cu", "stats.cu", "nphj.cu", "partition.cu", "phj.cu", "batch.cu", "mlp.cu", "selector.cu", "noalloc.cu", "smj.cu", "groupby.cu"]
+SOURCES = ["abi.cu", "planner.cu", "profile.cu", "stats.cu", "nphj.cu", "partition.cu", "phj.cu", "batch.cu", "mlp.cu", "selector.cu", "noalloc.cu", "smj.cu", "groupby.cu", "chunks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

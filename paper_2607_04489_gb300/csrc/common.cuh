@@ -7,12 +7,14 @@
 #include <stdint.h>
 
 // Shape of the partitioned join: threads per CTA and build rows per
-// shared-memory table (the planner sizes partitions to half of that).
+// shared-memory table (the planner aims at 2048-4096 rows per partition; the
+// cap leaves room for the spread of hashed partition sizes around 4096, and
+// its table of 2 x 4608 slots of 8 bytes still lets three CTAs share an SM).
 #ifndef EIGER_JOIN_THREADS
 #define EIGER_JOIN_THREADS 512
 #endif
 #ifndef EIGER_BUILD_CAP
-#define EIGER_BUILD_CAP 4096
+#define EIGER_BUILD_CAP 4608
 #endif
 
 namespace eiger {

@@ -24,6 +24,7 @@ struct ProfScope {
 void prof_reset();
 void prof_set_matches(unsigned long long m);
 bool prof_set_enabled(bool on);  // returns the previous setting
+bool prof_enabled();
 double match_bytes(const JoinOut& out);
 
 // ------------------------------------------------------------------ streams
@@ -32,7 +33,9 @@ double match_bytes(const JoinOut& out);
 // of a call that can run beside the main stream (the build and probe sides'
 // partitioning). fork_side makes it wait for everything enqueued on `main`;
 // join_side makes `main` wait for everything enqueued on it. Created once per
-// host thread and device; no device memory is allocated.
+// host thread and device; no device memory is allocated. While per-launch
+// profiling is on, fork_side returns `main` itself, so every timed launch runs
+// alone and its events time that kernel only.
 cudaError_t fork_side(cudaStream_t main, cudaStream_t* side);
 cudaError_t join_side(cudaStream_t main, cudaStream_t side);
 
@@ -126,9 +129,28 @@ struct PartSide {
     size_t counts_len;
 };
 
+// Scratch of the compaction that follows a chunked pairs launch (chunks.cu).
+struct ChunkFix {
+    unsigned long long* hdr;  // [4]: moves, match count C, first run index at or above C, runs at or above C
+    uint32_t* hb_pref;        // [kMaxOutWarps + 1] holes below C per warp record, exclusive prefix
+    uint32_t* va_pref;        // [kMaxOutWarps + 2] filled positions at or above C per run, exclusive prefix
+    uint32_t* used_above;     // [kMaxOutWarps + 2] fill of every run at or above C
+};
+
+struct PairSink;
+ChunkFix chunk_fix_layout(Carve& c);
+// Makes the pairs of a chunked launch of W warps dense in [0, C) and sets the
+// cursor to C (two launches on `stream`).
+cudaError_t chunk_fix_run(const PairSink& s, uint32_t W, const ChunkFix& f, unsigned* err, const DevInfo& di,
+                          cudaStream_t stream);
+
 struct PhjScratch {
     PartSide side[2];
     unsigned long long* item_prefix;  // [P + 1]
+    // pairs output (chunks.cuh): warp records, overflow above the capacity, compaction scratch
+    void* rec;
+    uint32_t* ovf[2];
+    ChunkFix fix;
 };
 
 PhjScratch phj_layout(Carve& c, int64_t nb, int64_t np, const PlanDev& plan);

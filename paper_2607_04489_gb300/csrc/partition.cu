@@ -66,6 +66,11 @@ struct PartPass {
     const uint32_t* ntiles_dev;
     uint32_t ntiles_fixed;
     ColCarry cc;
+    // Exclusive ends of the memory a tile load may read around its rows (key
+    // source, tuple-ID source); the arrays' bases are the starts. A tile whose
+    // 16-byte aligned cover [align_down(first), align_up(last + 1)) lies
+    // inside is loaded by one bulk copy of the cover; nullptr: never.
+    const void* src_end[2];
 };
 
 template <typename InKey, typename KeyT>
@@ -144,9 +149,9 @@ __device__ uint32_t block_scan_smem(const uint32_t* in, uint32_t* out, uint32_t 
 template <typename InKey, typename KeyT, bool FIRST>
 struct PassIn {
     using E = typename std::conditional<FIRST, InKey, KeyT>::type;
-    static constexpr uint32_t kPad = 16 / sizeof(E);  // room for the 16-byte lead
+    static constexpr uint32_t kPad = 32 / sizeof(E);  // room for the 16-byte lead and tail of a cover copy
     static constexpr size_t kKeyBytes = align_up((kPartTile + kPad) * sizeof(E), 16);
-    static constexpr size_t kIdxBytes = FIRST ? 0 : align_up((kPartTile + 4) * sizeof(uint32_t), 16);
+    static constexpr size_t kIdxBytes = FIRST ? 0 : align_up((kPartTile + 8) * sizeof(uint32_t), 16);
     static constexpr size_t kBufBytes = kKeyBytes + kIdxBytes;
 };
 
@@ -178,6 +183,28 @@ struct TileRing {
     __device__ void issue(const PartPass<InKey, KeyT>& a, const Tile& tl, int b) const {
         const unsigned lane = lane_id();
         const E* kf = key_src(a, tl.start);
+        {
+            // The aligned cover of the tile inside the source arrays: one bulk
+            // copy per array, no element copies, no wait in this warp.
+            const E* kbase = FIRST ? reinterpret_cast<const E*>(a.raw) : reinterpret_cast<const E*>(a.in_key);
+            uint32_t kb = 0, ib = 0;
+            const char* kc = cover(kf, tl.len, kbase, a.src_end[0], kb);
+            const char* ic = nullptr;
+            bool ok = kc != nullptr;
+            if constexpr (ROWS) {
+                ic = cover(a.in_idx + tl.start, tl.len, a.in_idx, a.src_end[1], ib);
+                ok = ok && ic != nullptr;
+            }
+            if (ok) {
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&bar[b], kb + ib);
+                    bulk_load(keys(b), kc, kb, &bar[b]);
+                    if constexpr (ROWS) bulk_load(rows(b), ic, ib, &bar[b]);
+                }
+                return;
+            }
+        }
         uint32_t klead, klo, khi;
         uint32_t bytes = tile_copy_plan(kf, tl.len, klead, klo, khi);
         uint32_t ilead = 0, ilo = 0, ihi = 0;
@@ -196,6 +223,19 @@ struct TileRing {
         if constexpr (ROWS) edges_warp(rows(b), rf, tl.len, ilead, ilo, ihi, lane);
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar[b]);
+    }
+
+    // Start of the 16-byte aligned cover of [first, first + len) and its bytes
+    // (a multiple of 16), or nullptr when the cover leaves [base, end).
+    template <typename T>
+    __device__ static const char* cover(const T* first, uint32_t len, const T* base, const void* end,
+                                        uint32_t& bytes) {
+        if (!end) return nullptr;
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(first) & ~(uintptr_t)15;
+        const uintptr_t hi = (reinterpret_cast<uintptr_t>(first + len) + 15) & ~(uintptr_t)15;
+        if (lo < reinterpret_cast<uintptr_t>(base) || hi > reinterpret_cast<uintptr_t>(end)) return nullptr;
+        bytes = (uint32_t)(hi - lo);
+        return reinterpret_cast<const char*>(lo);
     }
 
     // Lane l of the issuing warp copies head element l and tail element l.
@@ -272,17 +312,20 @@ __device__ void ring_abort(const TileRing<InKey, KeyT, FIRST>& r, int other, uin
 
 template <typename InKey, typename KeyT, bool FIRST>
 __host__ __device__ constexpr size_t hist_smem_bytes(int bits) {
-    return align_up(16 + ((size_t)1 << bits) * sizeof(uint32_t), 16) +
+    return align_up(16 + 2 * ((size_t)1 << bits) * sizeof(uint32_t), 16) +
            2 * PassIn<InKey, KeyT, FIRST>::kBufBytes;
 }
 
+// Two CTA barriers per tile: the digit counters are double-buffered by tile
+// parity, so the next tile's counting starts while slower threads still store
+// this tile's counts.
 template <typename InKey, typename KeyT, bool FIRST, bool SORTM>
 __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey, KeyT> a, unsigned* err) {
     using Ring = TileRing<InKey, KeyT, FIRST>;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t nd = 1u << a.bits;
-    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + 16);
-    const Ring ring = ring_setup<InKey, KeyT, FIRST>(smem, align_up(16 + (size_t)nd * 4, 16));
+    uint32_t* s_cnt2 = reinterpret_cast<uint32_t*>(smem + 16);  // [2][nd]
+    const Ring ring = ring_setup<InKey, KeyT, FIRST>(smem, align_up(16 + 2 * (size_t)nd * 4, 16));
     __syncthreads();
     const uint32_t ntiles = a.tiles ? *a.ntiles_dev : a.ntiles_fixed;
     uint32_t t = blockIdx.x;
@@ -298,6 +341,7 @@ __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey,
             ring.template issue<false>(a, d_next, b ^ 1);
             if (tn + gridDim.x < ntiles) d_next = get_tile(a, tn + gridDim.x);
         }
+        uint32_t* s_cnt = s_cnt2 + b * nd;
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
         const Tile tl = get_tile(a, t);
         const bool ok = mbar_wait(&ring.bar[b], (it >> 1) & 1);
@@ -315,13 +359,12 @@ __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(PartPass<InKey,
         __syncthreads();
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x)
             a.counts[count_index(tl, t, d, a.bits)] = s_cnt[d];
-        __syncthreads();
     }
 }
 
 template <typename InKey, typename KeyT, bool FIRST>
 __host__ __device__ constexpr size_t scatter_smem_bytes(int bits) {
-    return align_up(16 + 3 * ((size_t)1 << bits) * sizeof(uint32_t), 16) +
+    return align_up(16 + 4 * ((size_t)1 << bits) * sizeof(uint32_t), 16) +
            2 * PassIn<InKey, KeyT, FIRST>::kBufBytes + align_up((size_t)kPartTile * sizeof(KeyT), 16) +
            (size_t)kPartTile * sizeof(uint32_t) + (size_t)kPartTile * sizeof(uint16_t);
 }
@@ -404,8 +447,13 @@ __device__ __forceinline__ void carry_columns(const ColCarry& cc, uint32_t tstar
     }
 }
 
+// The global digit offsets are double-buffered by tile parity, so no barrier
+// follows the write-out: the next tile stores its offsets into the other
+// buffer while slower threads still write the current tile out.
+// At most 64 registers (two CTAs per SM wherever shared memory allows; 64-bit
+// keys otherwise take ~100).
 template <typename InKey, typename KeyT, bool FIRST>
-__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InKey, KeyT> a, unsigned* err) {
+__global__ void __launch_bounds__(kPartThreads, 2) part_scatter_kernel(PartPass<InKey, KeyT> a, unsigned* err) {
     using Ring = TileRing<InKey, KeyT, FIRST>;
     using P = PassIn<InKey, KeyT, FIRST>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -415,8 +463,8 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
     const bool rows = a.out_idx != nullptr;  // tuple IDs travel with the keys
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + 16);
     uint32_t* s_start = s_cnt + nd;
-    uint32_t* s_goff = s_start + nd;
-    const size_t ring_off = align_up(16 + 3 * (size_t)nd * 4, 16);
+    uint32_t* s_goff2 = s_start + nd;  // [2][nd]
+    const size_t ring_off = align_up(16 + 4 * (size_t)nd * 4, 16);
     const Ring ring = ring_setup<InKey, KeyT, FIRST>(smem, ring_off);
     KeyT* s_key = reinterpret_cast<KeyT*>(smem + ring_off + 2 * P::kBufBytes);
     uint32_t* s_idx = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(s_key) +
@@ -450,6 +498,7 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
             issue_tile(ring, a, d_next, b ^ 1);
             if (tn + gridDim.x < ntiles) d_next = get_tile(a, tn + gridDim.x);
         }
+        uint32_t* s_goff = s_goff2 + b * nd;
         for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) s_cnt[d] = 0;
 #pragma unroll
         for (int q = 0; q < kGoffPerThread; ++q) {
@@ -509,6 +558,9 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
         }
         __syncthreads();
 
+        // No barrier after the write-out: the next tile stores its offsets
+        // into the other s_goff buffer, and its staging writes come after
+        // three more barriers, which every thread reaches only once done here.
         const uint32_t nk = s_kept;
         for (uint32_t pos = threadIdx.x; pos < nk; pos += blockDim.x) {
             const uint32_t d = s_dig[pos];
@@ -516,9 +568,11 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(PartPass<InK
             a.out_key[g] = s_key[pos];
             if (rows) a.out_idx[g] = s_idx[pos];
         }
-        __syncthreads();
         // carried columns reuse the key and row staging (contiguous, >= 8 bytes per row)
-        if (a.cc.n) carry_columns<false>(a.cc, tl.start, dr, nullptr, nd, s_start, s_goff, s_dig, nk, s_key);
+        if (a.cc.n) {
+            __syncthreads();
+            carry_columns<false>(a.cc, tl.start, dr, nullptr, nd, s_start, s_goff, s_dig, nk, s_key);
+        }
     }
 }
 
@@ -774,8 +828,11 @@ __global__ void __launch_bounds__(kScanThreads)
 
 // ------------------------------------------------------------ pass-2 tiling
 
-// One block. From the scanned pass-1 counts, the pass-1 partitions become the
-// pass-2 segments; each is cut into tiles of kPartTile rows.
+// From the scanned pass-1 counts, the pass-1 partitions become the pass-2
+// segments; each is cut into tiles of kPartTile rows. Every block scans the
+// (at most 2^kMaxBits) segment tile counts in shared memory itself; block 0
+// writes the segments and the tile count, and the blocks fill the tiles
+// grid-stride.
 __global__ void __launch_bounds__(1024)
     seg_tiles_kernel(const uint32_t* __restrict__ counts1, uint32_t ntiles1, int b1,
                      const uint32_t* __restrict__ total1, SegInfo* __restrict__ segs,
@@ -788,20 +845,23 @@ __global__ void __launch_bounds__(1024)
         const uint32_t st = ntiles1 ? counts1[(size_t)s * ntiles1] : 0u;
         const uint32_t en = s + 1 < nseg ? (ntiles1 ? counts1[(size_t)(s + 1) * ntiles1] : 0u) : *total1;
         const uint32_t sz = en - st;
-        segs[s].start = st;
-        segs[s].size = sz;
+        if (blockIdx.x == 0) {
+            segs[s].start = st;
+            segs[s].size = sz;
+        }
         s_nt[s] = (sz + kPartTile - 1) / kPartTile;
     }
     __syncthreads();
     const uint32_t total = block_scan_smem(s_nt, s_base, nseg, s_warp);
     __syncthreads();
-    for (uint32_t s = threadIdx.x; s < nseg; s += blockDim.x) {
-        segs[s].tile_base = s_base[s];
-        segs[s].ntiles = s_nt[s];
-    }
-    // every thread fills tiles; the segment of tile k is the last s with
-    // s_base[s] <= k among segments that have tiles (binary search in smem)
-    for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
+    if (blockIdx.x == 0)
+        for (uint32_t s = threadIdx.x; s < nseg; s += blockDim.x) {
+            segs[s].tile_base = s_base[s];
+            segs[s].ntiles = s_nt[s];
+        }
+    // the segment of tile k is the last s with s_base[s] <= k among segments
+    // that have tiles (binary search in shared memory)
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         uint32_t lo = 0, hi = nseg;
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
@@ -810,7 +870,8 @@ __global__ void __launch_bounds__(1024)
         // (an empty segment shares its base with the next one, so the last
         // segment whose base is <= k always has tiles)
         const uint32_t j = k - s_base[lo];
-        const uint32_t st = segs[lo].start, sz = segs[lo].size;
+        const uint32_t st = ntiles1 ? counts1[(size_t)lo * ntiles1] : 0u;
+        const uint32_t sz = (lo + 1 < nseg ? (ntiles1 ? counts1[(size_t)(lo + 1) * ntiles1] : 0u) : *total1) - st;
         Tile tl;
         tl.start = st + j * kPartTile;
         const uint32_t rest = sz - j * kPartTile;
@@ -820,7 +881,14 @@ __global__ void __launch_bounds__(1024)
         tl.ntiles_seg = s_nt[lo];
         tiles[k] = tl;
     }
-    if (threadIdx.x == 0) *ntiles2 = total;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ntiles2 = total;
+}
+
+// Blocks of seg_tiles_kernel for at most `max_tiles` pass-2 tiles.
+inline int seg_tiles_grid(size_t max_tiles, const DevInfo& di) {
+    const size_t g = (max_tiles + 4095) / 4096;
+    const size_t cap = (size_t)di.sms * 2;
+    return (int)(g < 1 ? 1 : g > cap ? cap : g);
 }
 
 // Start of every final partition, plus part_start[P] = rows kept.
@@ -941,6 +1009,7 @@ cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanD
 
     PartPass<InKey, KeyT> a{};
     a.raw = keys;
+    a.src_end[0] = keys + n;
     a.out_key = static_cast<KeyT*>(s.key[0]);
     a.out_idx = plan.no_rows ? nullptr : s.idx[0];
     a.n = n;
@@ -960,13 +1029,16 @@ cudaError_t partition_typed(const InKey* keys, uint32_t n, int side, const PlanD
     if (passes == 2) {
         {
             ProfScope ps("seg_tiles", 0.0, stream);
-            seg_tiles_kernel<<<1, 1024, 0, stream>>>(s.counts, ntiles1, b1, s.total, s.segs, s.tiles,
-                                                     s.total + 2);
+            const size_t max_tiles2 = (size_t)ntiles1 + ((size_t)1 << b1);
+            seg_tiles_kernel<<<seg_tiles_grid(max_tiles2, di), 1024, 0, stream>>>(s.counts, ntiles1, b1, s.total,
+                                                                                 s.segs, s.tiles, s.total + 2);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         PartPass<InKey, KeyT> b{};
         b.in_key = static_cast<const KeyT*>(s.key[0]);
         b.in_idx = plan.no_rows ? nullptr : s.idx[0];
+        b.src_end[0] = static_cast<const char*>(s.key[0]) + (size_t)n * sizeof(KeyT) + 16;
+        b.src_end[1] = s.idx[0] + (size_t)n + 4;
         b.out_key = static_cast<KeyT*>(s.key[1]);
         b.out_idx = plan.no_rows ? nullptr : s.idx[1];
         b.n = n;
@@ -1006,6 +1078,7 @@ cudaError_t sort_typed(const InKey* keys, uint32_t n, int side, const PlanDev& p
     cudaError_t e;
     PartPass<InKey, KeyT> a{};
     a.raw = keys;
+    a.src_end[0] = keys + n;
     a.out_key = static_cast<KeyT*>(s.key[0]);
     a.out_idx = plan.no_rows ? nullptr : s.idx[0];
     a.n = n;
@@ -1023,13 +1096,16 @@ cudaError_t sort_typed(const InKey* keys, uint32_t n, int side, const PlanDev& p
     if (passes < 2) return cudaSuccess;
     {
         ProfScope ps("seg_tiles", 0.0, stream);
-        seg_tiles_kernel<<<1, 1024, 0, stream>>>(s.counts, ntiles1, 0, s.total, s.segs, s.tiles, s.total + 2);
+        seg_tiles_kernel<<<seg_tiles_grid((size_t)ntiles1 + 1, di), 1024, 0, stream>>>(s.counts, ntiles1, 0, s.total,
+                                                                                     s.segs, s.tiles, s.total + 2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     for (int i = 1; i < passes; ++i) {
         PartPass<InKey, KeyT> b{};
         b.in_key = static_cast<const KeyT*>(s.key[(i - 1) & 1]);
         b.in_idx = plan.no_rows ? nullptr : s.idx[(i - 1) & 1];
+        b.src_end[0] = static_cast<const char*>(s.key[(i - 1) & 1]) + (size_t)n * sizeof(KeyT) + 16;
+        b.src_end[1] = s.idx[(i - 1) & 1] + (size_t)n + 4;
         b.out_key = static_cast<KeyT*>(s.key[i & 1]);
         b.out_idx = plan.no_rows ? nullptr : s.idx[i & 1];
         b.n = n;
@@ -1065,8 +1141,10 @@ void part_side_layout(Carve& c, PartSide& ps, int64_t n, int b1, int b2, int pas
     const int nbuf = passes < 2 ? passes : 2;
     const int ncols = plan.gftr ? plan.ncols[side] : 0;
     for (int k = 0; k < 2; ++k) {
-        ps.key[k] = k < nbuf ? c.take<unsigned char>((size_t)n * kb) : nullptr;
-        ps.idx[k] = k < nbuf ? c.take<uint32_t>((size_t)n) : nullptr;
+        // 16 bytes of slack after each buffer: a later pass's tile loads may
+        // read the aligned cover of the last rows (see PartPass::src_end)
+        ps.key[k] = k < nbuf ? c.take<unsigned char>((size_t)n * kb + 16) : nullptr;
+        ps.idx[k] = k < nbuf ? c.take<uint32_t>((size_t)n + 4) : nullptr;
         for (int q = 0; q < kMaxCols; ++q)
             ps.col[k][q] = (k < nbuf && q < ncols) ? c.take<unsigned char>((size_t)n * plan.col_bytes[side][q])
                                                   : nullptr;

@@ -6,15 +6,16 @@
 // Work item = (partition p, build chunk c_R, probe chunk c_S). A build
 // partition larger than one shared-memory table (duplicate-heavy keys) is cut
 // into chunks of at most kBuildCap rows, each joined with the whole probe
-// partition; a large probe partition (skew) is cut into chunks of kProbeChunk
-// rows so that hot partitions spread over many CTAs. A persistent grid pulls
-// items from a global counter. Per item a CTA clears a table of the next power
-// of two >= 2 x rows (load factor <= 0.5), inserts the build chunk with
-// shared-memory CAS, then streams the probe chunk, walking linear-probe chains
-// and emitting matches through the CTA stage (emit.cuh).
-//
-// Table slots use the low bits of the same mix(key') whose top bits chose the
-// partition, so slots are uniform within a partition.
+// partition; a large probe partition (skew) is cut into chunks of at most
+// kProbeChunk rows so that hot partitions spread over many CTAs. The chunks of
+// a partition are balanced in size. A persistent grid pulls
+// items from a global counter. Per item a CTA clears a table of about three
+// slots per build row (load factor <= 1/3), inserts the build chunk with
+// shared-memory CAS, then streams the probe chunk, walking linear-probe chains.
+// Index pairs leave through per-warp output runs (chunks.cuh), so the probe
+// loop has no CTA barrier; payloads, GFTR positions and aggregates go through
+// the CTA stage (emit.cuh).
+#include "chunks.cuh"
 #include "emit.cuh"
 #include "kernels.cuh"
 
@@ -26,19 +27,28 @@ size_t part_scan_blocks(size_t counts_len);
 namespace {
 
 constexpr int kJoinThreads = EIGER_JOIN_THREADS;
-constexpr int kJoinMinBlocks = 1024 / kJoinThreads;  // 64 registers per thread
-constexpr int kMaxRows = 8;                       // rows per thread per round (32-bit keys)
+constexpr int kMaxRows = 8;                       // rows per thread per round (at most)
 constexpr int kJoinStage = kJoinThreads * kMaxRows;  // a unique-key round never spills
 constexpr uint32_t kBuildCap = EIGER_BUILD_CAP;   // build rows per shared-memory table
 
-// Rows each thread keeps in flight per round: 8 for 32-bit keys, 4 for 64-bit
-// keys (register budget of two 512-thread CTAs per SM).
-template <typename KeyT>
+// Rows each thread keeps in flight per round (the current round and the next
+// one's loads) and CTAs per SM. Index pairs of 32-bit keys: 4 rows, three
+// 512-thread CTAs per SM (40 registers), so that while one CTA clears or builds
+// its table the others probe theirs (measured on GB300: 16 % faster than two
+// CTAs of 8 rows). Payload, position and aggregate outputs keep more live
+// state per match and 64-bit keys larger tables: two CTAs per SM, 8 rows for
+// 32-bit keys and 4 for 64-bit keys (64 registers).
+template <typename KeyT, bool PAIRS>
 struct Rows {
-    static constexpr int kN = sizeof(KeyT) == 4 ? 8 : 4;
+    static constexpr bool kLean = sizeof(KeyT) == 4 && PAIRS;
+    static constexpr int kN = kLean || sizeof(KeyT) != 4 ? 4 : 8;
+    static constexpr int kMinBlocks = (kLean ? 1536 : 1024) / kJoinThreads;
     static constexpr uint32_t kRound = kJoinThreads * kN;
 };
-constexpr uint32_t kProbeChunk = 16384;
+#ifndef EIGER_PROBE_CHUNK
+#define EIGER_PROBE_CHUNK 32768
+#endif
+constexpr uint32_t kProbeChunk = EIGER_PROBE_CHUNK;  // probe rows per work item, at most
 constexpr uint32_t kTableMax = 2 * kBuildCap;
 constexpr uint32_t kEmptyRow = 0xFFFFFFFFu;
 
@@ -124,16 +134,21 @@ template <typename KeyT>
 struct SmemTable;
 
 // Home slot of a key in a table of `tsize` slots. The partition was chosen by
-// the top bits of the hash, so the hash is first remixed by an odd multiplier
-// (which carries its low bits into the high bits) and then mapped onto
-// [0, tsize) by a multiply-shift range reduction.
+// the top bits of a mixed key, so the keys of one partition are a scattered
+// subset of the key space; a Fibonacci (multiplicative) hash of the key itself
+// spreads them over the table, and a multiply-shift range reduction maps its
+// top bits onto [0, tsize).
 // Slots come in aligned pairs: the home slot is even, so a probe reads its
 // first two candidates with one 16-byte shared load (inserts are ordinary
 // linear probing from the same home slot, filling a pair's first slot first).
+__device__ __forceinline__ uint32_t slot_hash(uint32_t k) { return k * 0x9E3779B1u; }
+__device__ __forceinline__ uint32_t slot_hash(uint64_t k) {
+    return (uint32_t)((k * 0x9E3779B97F4A7C15ull) >> 32);
+}
+
 template <typename KeyT>
 __device__ __forceinline__ uint32_t home_slot(KeyT k, uint32_t tsize) {
-    const uint32_t h = (uint32_t)KeyCodec<KeyT>::hash(k) * 0x9E3779B1u;
-    return 2u * (uint32_t)(((unsigned long long)h * (tsize >> 1)) >> 32);
+    return 2u * (uint32_t)(((unsigned long long)slot_hash(k) * (tsize >> 1)) >> 32);
 }
 
 __device__ __forceinline__ uint32_t next_slot(uint32_t s, uint32_t tsize) {
@@ -146,7 +161,11 @@ struct SmemTable<uint32_t> {
     static constexpr size_t kSlotBytes = 8;
     unsigned long long* slot;
     __device__ void bind(unsigned char* smem) { slot = reinterpret_cast<unsigned long long*>(smem); }
-    __device__ void clear(uint32_t i) { slot[i] = kEmptySlot; }
+    // every slot of a table of tsize (a multiple of 2) slots, two per 16-byte store
+    __device__ void clear_all(uint32_t tsize) {
+        ulonglong2* p = reinterpret_cast<ulonglong2*>(slot);
+        for (uint32_t i = threadIdx.x; i < tsize / 2; i += blockDim.x) p[i] = make_ulonglong2(kEmptySlot, kEmptySlot);
+    }
     // 1: inserted; 0: slot taken by another key; -1: slot taken by the same key
     __device__ int insert(uint32_t s, uint32_t k, uint32_t row) {
         const unsigned long long prev = atomicCAS(slot + s, kEmptySlot, ((unsigned long long)k << 32) | row);
@@ -174,14 +193,21 @@ struct SmemTable<uint64_t> {
         key = reinterpret_cast<unsigned long long*>(smem);
         row = reinterpret_cast<uint32_t*>(smem + (size_t)kTableMax * 8);
     }
-    __device__ void clear(uint32_t i) { row[i] = kEmptyRow; }
+    __device__ void clear_all(uint32_t tsize) {
+        for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) row[i] = kEmptyRow;
+    }
     // 1: inserted; 0: slot taken (its key may still be in flight, so equal
-    // keys are not detected here: 64-bit tables always take the general path)
+    // keys are not detected here but by has_equal_keys after the build)
     __device__ int insert(uint32_t s, uint64_t k, uint32_t r) {
         if (atomicCAS(row + s, kEmptyRow, r) != kEmptyRow) return 0;
         key[s] = k;
         return 1;
     }
+    // After every insert has completed: 1 when an occupied slot of this
+    // thread's share finds its own key earlier in its probe chain, i.e. the
+    // table holds a key twice. Linear probing leaves no empty slot between a
+    // key's home slot and its slot, so each walk is short and bounded.
+    __device__ int has_equal_keys(uint32_t tsize) const;
     __device__ int probe(uint32_t s, uint64_t k, uint32_t& r) const {
         const uint32_t v = row[s];
         if (v == kEmptyRow) return 0;
@@ -190,22 +216,33 @@ struct SmemTable<uint64_t> {
     }
 };
 
+__device__ int SmemTable<uint64_t>::has_equal_keys(uint32_t tsize) const {
+    for (uint32_t s = threadIdx.x; s < tsize; s += blockDim.x) {
+        if (row[s] == kEmptyRow) continue;
+        const uint64_t k = key[s];
+        uint32_t t = home_slot(k, tsize);
+        for (uint32_t n = 0; t != s && n < tsize; ++n, t = next_slot(t, tsize))
+            if (key[t] == k) return 1;
+    }
+    return 0;
+}
+
 // Rows of a probe round: kRows per thread, strided by the block size so every
 // load instruction of a warp reads 32 consecutive rows.
-template <typename KeyT>
+template <typename KeyT, int N>
 struct RoundRegs {
-    KeyT k[Rows<KeyT>::kN];
-    uint32_t id[Rows<KeyT>::kN];
+    KeyT k[N];
+    uint32_t id[N];
 };
 
 // POS (GFTR): a row is identified by its position in the partitioned arrays
 // (pos0 + i), not by the tuple ID stored beside its key.
-template <bool POS, typename KeyT>
-__device__ __forceinline__ void load_round(RoundRegs<KeyT>& r, const KeyT* __restrict__ key,
+template <bool POS, typename KeyT, int N>
+__device__ __forceinline__ void load_round(RoundRegs<KeyT, N>& r, const KeyT* __restrict__ key,
                                            const uint32_t* __restrict__ idx, uint32_t base,
                                            uint32_t n, uint32_t pos0) {
 #pragma unroll
-    for (int j = 0; j < Rows<KeyT>::kN; ++j) {
+    for (int j = 0; j < N; ++j) {
         const uint32_t i = base + j * kJoinThreads + threadIdx.x;
         if (i < n) {
             r.k[j] = __ldcs(key + i);
@@ -244,7 +281,7 @@ constexpr int kJoinWarps = kJoinThreads / kWarp;
 // Thread t reads back only its own stage entries, so no barrier precedes the
 // ballots: the previous round's closing barrier already orders every read of
 // s_grp before the new counts are written.
-template <int kN, bool PAIRS>
+template <int kN>
 __device__ __forceinline__ void flush_positional(Stage<kJoinStage>& st, uint32_t* s_grp,
                                                  const JoinOut& out, Ctrl* ctrl) {
     const unsigned lane = lane_id();
@@ -294,32 +331,35 @@ __device__ __forceinline__ void flush_positional(Stage<kJoinStage>& st, uint32_t
         const uint32_t i = j * kJoinThreads + threadIdx.x;
         if (ball[j] & (1u << lane)) {
             const unsigned long long pos = base + s_grp[j * kJoinWarps + w] + __popc(ball[j] & lt);
-            if (PAIRS && fits) {
-                __stcs(out.bidx + pos, st.b[i]);
-                __stcs(out.pidx + pos, st.p[i]);
-            } else {
-                write_match(out, pos, st.b[i], st.p[i]);
-            }
+            (void)fits;
+            write_match(out, pos, st.b[i], st.p[i]);
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) st.count = 0;
 }
 
+// PAIRS: index pairs only, written through per-warp output runs (chunks.cuh)
+// without any CTA barrier in the probe loop; otherwise matches go through the
+// CTA stage (emit.cuh), which also gathers payloads, maps positions back to
+// tuple IDs (GFTR) or aggregates.
 template <typename KeyT, bool AGG, bool PAIRS, bool POS>
-__global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
-    phj_join_kernel(JoinIn<KeyT> a, JoinOut out, Ctrl* ctrl) {
+__global__ void __launch_bounds__(kJoinThreads, (Rows<KeyT, PAIRS>::kMinBlocks))
+    phj_join_kernel(JoinIn<KeyT> a, JoinOut out, PairSink sink, Ctrl* ctrl) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Stage<kJoinStage> st;
+    // the stage follows the table in dynamic shared memory (none with PAIRS)
+    Stage<kJoinStage>& st = *reinterpret_cast<Stage<kJoinStage>*>(smem + (size_t)kTableMax * SmemTable<KeyT>::kSlotBytes);
     __shared__ uint32_t s_grp[kMaxRows * kJoinWarps];
     __shared__ unsigned long long s_next_item;
     __shared__ uint32_t s_next_part;
-    constexpr int kN = Rows<KeyT>::kN;
-    constexpr uint32_t kRound = Rows<KeyT>::kRound;
+    constexpr int kN = Rows<KeyT, PAIRS>::kN;
+    constexpr uint32_t kRound = Rows<KeyT, PAIRS>::kRound;
     SmemTable<KeyT> tab;
     tab.bind(smem);
-    if (threadIdx.x == 0) st.count = 0;
+    if (!PAIRS && threadIdx.x == 0) st.count = 0;
     AggState agg{0ull, 0ull};
+    WarpChunk wc;
+    wc.init();
     const unsigned long long nitems = ctrl->nitems;
 
     // Work items are claimed one ahead: the claim for the next item is issued
@@ -347,14 +387,19 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
         const uint32_t bs0 = a.bstart[p], bsz = a.bstart[p + 1] - bs0;
         const uint32_t ps0 = a.pstart[p], psz = a.pstart[p + 1] - ps0;
         const uint32_t npc = (psz + kProbeChunk - 1) / kProbeChunk;
-        const unsigned long long local = item - a.item_prefix[p];
-        const uint32_t bc = (uint32_t)(local / npc), pc = (uint32_t)(local % npc);
-        const uint32_t bn = bsz - bc * kBuildCap < kBuildCap ? bsz - bc * kBuildCap : kBuildCap;
-        const uint32_t pn = psz - pc * kProbeChunk < kProbeChunk ? psz - pc * kProbeChunk : kProbeChunk;
-        const KeyT* bkey = a.bkey + bs0 + bc * kBuildCap;
-        const uint32_t* bidx = a.bidx + bs0 + bc * kBuildCap;
-        const KeyT* pkey = a.pkey + ps0 + pc * kProbeChunk;
-        const uint32_t* pidx = a.pidx + ps0 + pc * kProbeChunk;
+        const uint32_t local = (uint32_t)(item - a.item_prefix[p]);  // < items of one partition
+        const uint32_t bc = local / npc, pc = local - bc * npc;
+        // chunks of a partition are balanced (sizes differ by at most one
+        // row), so no item joins a full table with a sliver of probe rows
+        const uint32_t nbc = (bsz + kBuildCap - 1) / kBuildCap;
+        const uint32_t b_lo = (uint32_t)((unsigned long long)bc * bsz / nbc);
+        const uint32_t bn = (uint32_t)((unsigned long long)(bc + 1) * bsz / nbc) - b_lo;
+        const uint32_t p_lo = (uint32_t)((unsigned long long)pc * psz / npc);
+        const uint32_t pn = (uint32_t)((unsigned long long)(pc + 1) * psz / npc) - p_lo;
+        const KeyT* bkey = a.bkey + bs0 + b_lo;
+        const uint32_t* bidx = a.bidx + bs0 + b_lo;
+        const KeyT* pkey = a.pkey + ps0 + p_lo;
+        const uint32_t* pidx = a.pidx + ps0 + p_lo;
         // about three slots per build row (load <= 1/3), at most kTableMax
         uint32_t tsize = (3 * bn + 31) & ~31u;
         if (tsize < 64) tsize = 64;
@@ -362,15 +407,15 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
 
         // Issue the first build and probe loads before clearing the table, so
         // their latency overlaps the clear.
-        RoundRegs<KeyT> cur, nxt;
-        const uint32_t bpos0 = bs0 + bc * kBuildCap, ppos0 = ps0 + pc * kProbeChunk;
+        RoundRegs<KeyT, kN> cur, nxt;
+        const uint32_t bpos0 = bs0 + b_lo, ppos0 = ps0 + p_lo;
         load_round<POS>(nxt, bkey, bidx, 0, bn, bpos0);
         load_round<POS>(cur, pkey, pidx, 0, pn, ppos0);
-        for (uint32_t i = threadIdx.x; i < tsize; i += kJoinThreads) tab.clear(i);
+        tab.clear_all(tsize);
         __syncthreads();
         // Build. An insert that meets its own key proves a duplicate in this
         // chunk; without one, every probe key has at most one match here.
-        int dup = sizeof(KeyT) != 4;  // 64-bit tables cannot see equal keys in flight
+        int dup = 0;
         for (uint32_t bb = 0; bb < bn; bb += kRound) {
             if (bb) load_round<POS>(nxt, bkey, bidx, bb, bn, bpos0);
 #pragma unroll
@@ -388,6 +433,10 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
                     s = next_slot(s, tsize);
                 }
             }
+        }
+        if constexpr (sizeof(KeyT) != 4) {
+            __syncthreads();  // every key of the table is written
+            dup = tab.has_equal_keys(tsize);
         }
         const bool unique = __syncthreads_or(dup) == 0;
         if (threadIdx.x < kWarp) {  // look up the next item while the probes run
@@ -438,7 +487,9 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
                             }
                         }
                     }
-                    if (AGG) {
+                    if constexpr (PAIRS) {
+                        warp_emit(wc, sink, brow != kHole, brow, cur.id[j]);
+                    } else if constexpr (AGG) {
                         if (brow != kHole) {
                             agg.sum += (unsigned long long)read_pay(out.b.src[0], out.b.bytes[0], brow) +
                                        (unsigned long long)read_pay(out.p.src[0], out.p.bytes[0], cur.id[j]);
@@ -449,7 +500,7 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
                         st.p[j * kJoinThreads + threadIdx.x] = cur.id[j];
                     }
                 }
-                if (!AGG) flush_positional<kN, PAIRS>(st, s_grp, out, ctrl);
+                if constexpr (!AGG && !PAIRS) flush_positional<kN>(st, s_grp, out, ctrl);
             } else {
                 // General path (duplicate keys): every match of every chain,
                 // emitted through the warp-aggregated stage.
@@ -473,21 +524,25 @@ __global__ void __launch_bounds__(kJoinThreads, kJoinMinBlocks)
                                 if (++steps == tsize) active = false;
                             }
                         }
-                        emit<AGG, kJoinStage>(st, agg, hit, brow, id, out, &ctrl->cursor);
+                        if constexpr (PAIRS)
+                            warp_emit(wc, sink, hit, brow, id);
+                        else
+                            emit<AGG, kJoinStage>(st, agg, hit, brow, id, out, &ctrl->cursor);
                     }
                 }
-                stage_flush<AGG, kJoinStage>(st, out, &ctrl->cursor);
+                if constexpr (!PAIRS) stage_flush<AGG, kJoinStage>(st, out, &ctrl->cursor);
             }
             cur = nxt;
         }
         __syncthreads();
     }
     if (AGG) agg_commit(agg, ctrl);
+    if constexpr (PAIRS) warp_chunk_commit(wc, sink, blockIdx.x * kJoinWarps + threadIdx.x / kWarp);
 }
 
 template <typename KeyT>
-size_t join_smem() {
-    return (size_t)kTableMax * SmemTable<KeyT>::kSlotBytes;
+size_t join_smem(bool pairs) {
+    return (size_t)kTableMax * SmemTable<KeyT>::kSlotBytes + (pairs ? 0 : sizeof(Stage<kJoinStage>));
 }
 
 template <typename KeyT>
@@ -520,15 +575,28 @@ cudaError_t launch_join(const PhjScratch& s, const PlanDev& plan, const JoinOut&
                  pos_agg ? (double)sizeof(KeyT) * (double)(nb + np) + (double)out.b.bytes[0] * (double)nb
                          : tuple * (double)(nb + np),
                  stream, pos_agg ? (double)out.p.bytes[0] : match_bytes(out));
-    const size_t smem = join_smem<KeyT>();
+    const size_t smem = join_smem<KeyT>(pairs);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kJoinThreads, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    kern<<<di.sms * per_sm, kJoinThreads, smem, stream>>>(a, out, ctrl);
-    return cudaGetLastError();
+    uint32_t grid = (uint32_t)(di.sms * per_sm);
+    if (grid > kMaxOutWarps / kJoinWarps) grid = kMaxOutWarps / kJoinWarps;  // warp records of the pairs sink
+    PairSink sink{};
+    if (pairs) {
+        sink.bidx = out.bidx;
+        sink.pidx = out.pidx;
+        sink.capacity = out.capacity;
+        sink.ovf_b = s.ovf[0];
+        sink.ovf_p = s.ovf[1];
+        sink.cursor = &ctrl->cursor;
+        sink.rec = static_cast<ChunkRec*>(s.rec);
+    }
+    kern<<<grid, kJoinThreads, smem, stream>>>(a, out, sink, ctrl);
+    if ((e = cudaGetLastError()) != cudaSuccess || !pairs) return e;
+    return chunk_fix_run(sink, grid * kJoinWarps, s.fix, &ctrl->err, di, stream);
 }
 
 }  // namespace
@@ -542,6 +610,10 @@ PhjScratch phj_layout(Carve& c, int64_t nb, int64_t np, const PlanDev& plan) {
     part_side_layout(c, s.side[0], nb, b1, b2, passes, false, kb, plan, 0);
     part_side_layout(c, s.side[1], np, b1, b2, passes, false, kb, plan, 1);
     s.item_prefix = c.take<unsigned long long>(P + 1);
+    s.rec = c.take<ChunkRec>(kMaxOutWarps);
+    s.ovf[0] = c.take<uint32_t>((size_t)kMaxOutWarps * kOutChunk);
+    s.ovf[1] = c.take<uint32_t>((size_t)kMaxOutWarps * kOutChunk);
+    s.fix = chunk_fix_layout(c);
     return s;
 }
 

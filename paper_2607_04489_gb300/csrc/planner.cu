@@ -11,14 +11,19 @@
 //    tuples;
 //  - NPHJ while its table (load factor 0.5) fits half of the L2 cache;
 //  - otherwise PHJ with enough radix bits that an average build partition
-//    holds at most half a shared-memory table (kTargetRows), or three
-//    quarters of one when the HyperLogLog estimate says the build keys are
-//    all distinct (kTargetRowsDistinct), in one pass up to kOnePassBits bits
-//    and in two balanced passes beyond (pass 2 takes an odd count's extra
-//    bit). Measured on GB300: with unique build
-//    keys, partitions of 2300-3000 rows beat 1100-1500 rows by 2-16 % (pairs
-//    and the fused sum alike, 4.7M to 150M build rows); with duplicate build
-//    keys the smaller partitions win by 11-16 % (3000 timed joins).
+//    holds at most kTargetRows rows, or kTargetRowsDistinct when the
+//    HyperLogLog estimate says the build keys are all distinct
+//    (kTargetRowsDistinctLarge from kLargeBuild rows up), in one pass up to
+//    kOnePassBits bits and in two balanced passes beyond (pass 2 takes an odd
+//    count's extra bit). Measured on GB300: with unique build keys,
+//    partitions of 2300-3000 rows beat 1100-1500 rows by 2-16 % (pairs and the
+//    fused sum alike, 4.7M to 150M build rows); with duplicate build keys the
+//    smaller partitions win by 11-16 % (3000 timed joins). From 2^27 unique
+//    rows up, 4096-row partitions win (2^27 x 2^29: 13.7 against 14.1 ms;
+//    2^28 x 2^30: 31.1 against 34.8 ms): they keep the second pass at 256
+//    digits where 2048-3072-row partitions need 512, whose 8-row digit runs
+//    and doubled count arrays slow that pass by a third; below 2^27 they lose
+//    (2^24: 1.81 against 1.72 ms).
 #include <algorithm>
 #include <cmath>
 
@@ -28,8 +33,11 @@
 namespace eiger {
 
 namespace {
-constexpr int64_t kTargetRows = EIGER_BUILD_CAP / 2;  // average build rows per partition
-constexpr int64_t kTargetRowsDistinct = 3 * EIGER_BUILD_CAP / 4;  // ... when the build keys are distinct
+constexpr int64_t kTargetRows = 2048;           // average build rows per partition
+constexpr int64_t kTargetRowsDistinct = 3072;   // ... when the build keys are distinct
+constexpr int64_t kTargetRowsDistinctLarge = 4096;  // ... from kLargeBuild build rows up
+constexpr int64_t kLargeBuild = 1ll << 27;
+static_assert(kTargetRowsDistinctLarge < EIGER_BUILD_CAP, "an average partition fits one table");
 constexpr double kDistinctFraction = 0.9;  // estimate / rows above which the keys count as distinct
 constexpr int kOnePassBits = 8;
 constexpr int kMaxTotalBits = 20;
@@ -40,7 +48,7 @@ bool distinct_keys(double estimate, int64_t nb) {
 }
 
 int phj_total_bits(int64_t nb, bool distinct) {
-    const int64_t target = distinct ? kTargetRowsDistinct : kTargetRows;
+    const int64_t target = !distinct ? kTargetRows : nb >= kLargeBuild ? kTargetRowsDistinctLarge : kTargetRowsDistinct;
     const int64_t parts = (nb + target - 1) / target;
     int b = 0;
     while ((1ll << b) < parts) ++b;

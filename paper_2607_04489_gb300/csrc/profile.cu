@@ -76,6 +76,8 @@ double match_bytes(const JoinOut& out) {
 }
 int prof_count() { return g_prof.used; }
 
+bool prof_enabled() { return g_prof.enabled; }
+
 bool prof_set_enabled(bool on) {
     const bool was = g_prof.enabled;
     g_prof.enabled = on;

@@ -69,10 +69,10 @@ eiger_plan_t class_plan(int cls) {
         p.variant = EIGER_PHJ1;
         p.bits1 = 7 + cls;  // 8..12
     } else {
-        const int B = 4 + cls;  // 10..18
+        const int B = 4 + cls;  // 10..18, split like the rules: pass 2 takes an odd count's extra bit
         p.variant = EIGER_PHJ2;
-        p.bits1 = (B + 1) / 2;
-        p.bits2 = B / 2;
+        p.bits1 = B / 2;
+        p.bits2 = B - B / 2;
     }
     return p;
 }

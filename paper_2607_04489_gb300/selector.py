@@ -38,7 +38,7 @@ CLASSES = eiger.MLP_OUT
 COST_CAP = 4.0             # relative slowdown assigned to unmeasured (dominated) classes
 PROBE_SAMPLE = 1 << 20     # probe rows profiled for the features
 MAX_MATCHES = 1 << 30      # joins with larger outputs are redrawn
-BUILD_CAP = 4096           # rows per shared-memory table of the partitioned join
+BUILD_CAP = 4608           # rows per shared-memory table of the partitioned join
 
 COLUMNS = (["seed", "dtype", "nb", "np", "matches"] + [f"f{i}" for i in range(eiger.MLP_IN)] +
            [f"t{c}" for c in range(CLASSES)] + ["t_rules", "rules_class"])

@@ -69,7 +69,8 @@ def test_planner_large_build_partitions_in_two_passes(lib):
 
 def test_planner_distinct_build_keys_get_larger_partitions(lib):
     """All-distinct build keys (HyperLogLog estimate >= 0.9 x rows) aim at up
-    to 3072 rows per partition, duplicate-heavy ones at up to 2048."""
+    to 3072 rows per partition (4096 from 2^27 rows up), duplicate-heavy ones
+    at up to 2048."""
     nb = 150_000_000
     uniq = lib.plan(_stats(nb, 1, nb), None, nb, 4 * nb, lib.I32)
     dups = lib.plan(_stats(nb, 1, nb, est=nb / 10), None, nb, 4 * nb, lib.I32)
@@ -80,18 +81,27 @@ def test_planner_distinct_build_keys_get_larger_partitions(lib):
         assert p.bits1 + p.bits2 == 15
     assert lib.plan(_stats(1 << 20, 0, 1 << 30, est=0.89 * (1 << 20)), None, 1 << 20, 1 << 22,
                     lib.I64).variant == "nphj"
+    # 2^28 rows: 4096-row partitions for distinct keys (16 bits, 256 digits per
+    # pass), 2048 for duplicate-heavy ones (17 bits)
+    big_u = lib.plan(_stats(1 << 28, 0, (1 << 28) - 1), None, 1 << 28, 1 << 30, lib.I64)
+    big_d = lib.plan(_stats(1 << 28, 0, (1 << 28) - 1, est=1 << 24), None, 1 << 28, 1 << 30, lib.I64)
+    assert (big_u.bits1, big_u.bits2) == (8, 8) and (big_d.bits1, big_d.bits2) == (8, 9)
+
+
+def _target(nb, distinct):
+    return (4096 if nb >= 1 << 27 else 3072) if distinct else 2048
 
 
 def _rules_reference(nb, distinct, key32, l2=126 << 20):
     """The planning rules restated from their specification (Sec. 5.2.1-5.2.2
-    crossover; partition target 2048 rows, 3072 for distinct build keys):
-    (variant, bits1, bits2)."""
+    crossover; partition target 2048 rows, 3072 for distinct build keys, 4096
+    for distinct build keys from 2^27 rows up): (variant, bits1, bits2)."""
     slots = 64
     while slots < nb / 0.5:
         slots <<= 1
     if slots * (8 if key32 else 16) <= l2 // 2:
         return ("nphj", None, None)
-    target = 3072 if distinct else 2048
+    target = _target(nb, distinct)
     parts = (nb + target - 1) // target
     b = max(2, min(20, (parts - 1).bit_length()))  # smallest b with 2^b >= parts
     if b <= 8:
@@ -114,8 +124,8 @@ def test_planner_matches_its_rules_everywhere(lib, log2nb, scale, distinct):
     assert got == want
     if p.variant != "nphj":
         b = p.bits1 + p.bits2
-        assert nb / (1 << b) <= (3072 if distinct else 2048) or b == 20
-        assert b == 2 or nb / (1 << (b - 1)) > (3072 if distinct else 2048)
+        assert nb / (1 << b) <= _target(nb, distinct) or b == 20
+        assert b == 2 or nb / (1 << (b - 1)) > _target(nb, distinct)
 
 
 def test_planner_narrows_only_spans_below_2_32(lib):
