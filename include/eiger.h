@@ -134,15 +134,20 @@ eiger_status eiger_stats(const void* d_keys, int64_t n, eiger_dtype dtype, eiger
  * eiger_plan -- the rule-based selector and knob tuner (Sec. 1: statistics drive
  * algorithm selection and knob tuning; Table 1: relation cardinalities and the
  * key distribution decide). Host-only; launches nothing, needs no GPU.
- * build/probe: statistics of the two key columns (probe may be NULL: only its
- *          size np is then used).
+ * build/probe: statistics of the build key column and of a probe sample
+ *          (probe may be NULL: only the probe size np is then used; eiger_join
+ *          profiles the first 2^20 probe rows when the rules would partition
+ *          32-bit keys and np >= 2 nb).
  * out:     the chosen plan (variant never EIGER_AUTO; selector = 0): NPHJ
- *          while its table (load factor 0.5) fits half the L2 cache; else PHJ
- *          with the fewest radix bits that keep an average build partition at
- *          or below 2048 rows (3072 when build->estimate >= 0.9 nb, i.e. the
- *          keys are distinct), in one pass up to 8 bits, else in two passes
- *          with an odd count's extra bit in the second; narrow = 1 when the
- *          build range spans < 2^32.
+ *          while its table (load factor 0.5) fits half the L2 cache, or, for
+ *          32-bit keys with np >= 2 nb, when the probe sample is heavily
+ *          skewed (probe->estimate / probe->n < 0.1, or < 0.5 with the table
+ *          within 4x the L2 cache); else PHJ with the fewest radix bits that
+ *          keep an average build partition at or below 2048 rows (3072 when
+ *          build->estimate >= 0.9 nb, i.e. the keys are distinct; 4096 for
+ *          distinct keys from 2^27 rows up), in one pass up to 8 bits, else in
+ *          two passes with an odd count's extra bit in the second; narrow = 1
+ *          when the build range spans < 2^32.
  * Errors: INVALID_ARG.
  */
 eiger_status eiger_plan(const eiger_stats_t* build, const eiger_stats_t* probe, int64_t nb,

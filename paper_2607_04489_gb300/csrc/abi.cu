@@ -53,7 +53,38 @@ struct SideStreams {
 };
 thread_local SideStreams g_side;
 
+// Page-locked host staging for the small results a call reads back (the
+// statistics, the control block): a copy into pageable memory goes through a
+// driver staging buffer and costs a few microseconds more per call. One
+// buffer per host thread, allocated on first use and kept until exit; on
+// failure the caller's pageable destination is used directly.
+constexpr size_t kStageBytes = 32 << 10;
+thread_local void* g_host_stage = nullptr;
+thread_local bool g_host_stage_failed = false;
+
+void* host_stage(size_t bytes) {
+    if (bytes > kStageBytes || g_host_stage_failed) return nullptr;
+    if (!g_host_stage) {
+        if (cudaHostAlloc(&g_host_stage, kStageBytes, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            g_host_stage = nullptr;
+            g_host_stage_failed = true;
+        }
+    }
+    return g_host_stage;
+}
+
 }  // namespace
+
+// Device-to-host copy of a small result on `stream`, then a synchronisation
+// of the stream; through the page-locked staging buffer when it exists.
+cudaError_t readback_sync(void* dst, const void* src, size_t bytes, cudaStream_t stream) {
+    void* st = host_stage(bytes);
+    cudaError_t e = cudaMemcpyAsync(st ? st : dst, src, bytes, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess && st) std::memcpy(dst, st, bytes);
+    return e;
+}
 
 cudaError_t fork_side(cudaStream_t main, cudaStream_t* side) {
     if (prof_enabled()) {
@@ -137,9 +168,7 @@ eiger_status run_stats(const void* keys, int64_t n, int dtype, const StatsScratc
     }
     EIGER_CUDA(stats_launch(keys, n, dtype, ss, stream), "statistics kernels");
     static thread_local StatsDev host;
-    EIGER_CUDA(cudaMemcpyAsync(&host, ss.out, sizeof(StatsDev), cudaMemcpyDeviceToHost, stream),
-               "statistics readback");
-    EIGER_CUDA(cudaStreamSynchronize(stream), "statistics synchronise");
+    EIGER_CUDA(readback_sync(&host, ss.out, sizeof(StatsDev), stream), "statistics readback");
     out->min = host.mn;
     out->max = host.mx;
     std::memcpy(out->hll, host.regs, sizeof out->hll);
@@ -318,7 +347,8 @@ eiger_status validate_common(const JoinCall& c) {
 void sort_passes(eiger_plan_t* p);
 
 // Resolves the plan. `bst` holds the build statistics (NULL for STATIC).
-eiger_status resolve_plan(const JoinCall& c, const eiger_stats_t* bst, eiger_plan_t* pub) {
+eiger_status resolve_plan(const JoinCall& c, const eiger_stats_t* bst, eiger_plan_t* pub,
+                          double probe_distinct = -1.0) {
     if (c.variant == EIGER_STATIC) {
         *pub = static_plan();
         return check_plan(*pub, c.nb, c.dtype, false);
@@ -332,7 +362,7 @@ eiger_status resolve_plan(const JoinCall& c, const eiger_stats_t* bst, eiger_pla
         pub->selector = 2;
     } else {
         *pub = plan_rules(c.variant, c.nb, c.np, c.dtype, nok, distinct_keys(bst->estimate, c.nb),
-                          l2_bytes_or_default());
+                          l2_bytes_or_default(), probe_distinct);
     }
     if (c.dtype == EIGER_I32) pub->narrow = 1;  // int32 keys always travel as 32-bit offsets
     eiger_status s = check_plan(*pub, c.nb, c.dtype, nok);
@@ -471,6 +501,17 @@ eiger_status run_join(const JoinCall& c) {
     if (!chosen) {
         s = resolve_plan(c, adaptive ? &bst : nullptr, &pub);
         if (s != EIGER_OK) return s;
+        // a partitioned plan for a probe side at least twice the build side
+        // looks at a probe sample first: heavy skew favours the NPHJ
+        if (c.variant == EIGER_AUTO && !c.knobs &&
+            wants_probe_sample(pub, c.nb, c.np, c.dtype, narrowable(c.dtype, c.nb, bst.min, bst.max))) {
+            static thread_local eiger_stats_t pst;
+            const int64_t ns = c.np < kProbeSampleRows ? c.np : kProbeSampleRows;
+            s = run_stats(c.pkeys, ns, c.dtype, lay.stats, c.stream, &pst);
+            if (s != EIGER_OK) return s;
+            s = resolve_plan(c, &bst, &pub, pst.estimate / (double)ns);
+            if (s != EIGER_OK) return s;
+        }
     }
     s = resolve_materialize(c, adaptive ? &bst : nullptr, &pub);
     if (s != EIGER_OK) return s;
@@ -506,9 +547,7 @@ eiger_status run_join(const JoinCall& c) {
         EIGER_CUDA(phj_run(a, pd, ps, c.out, lay.ctrl, c.stream), "partitioned join");
 
     Ctrl h;
-    EIGER_CUDA(cudaMemcpyAsync(&h, lay.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c.stream),
-               "result readback");
-    EIGER_CUDA(cudaStreamSynchronize(c.stream), "join synchronise");
+    EIGER_CUDA(readback_sync(&h, lay.ctrl, sizeof(Ctrl), c.stream), "result readback");
     if (h.err & kErrTableFull) return fail(EIGER_ERR_TABLE_FULL, "a hash-table probe sequence hit its cap");
     if (h.err & kErrInternal) return fail(EIGER_ERR_INTERNAL, "device consistency check failed");
     prof_set_matches(h.cursor);
@@ -645,13 +684,14 @@ eiger_status eiger_stats(const void* d_keys, int64_t n, eiger_dtype dtype, eiger
 
 eiger_status eiger_plan(const eiger_stats_t* build, const eiger_stats_t* probe, int64_t nb, int64_t np,
                         eiger_dtype dtype, eiger_plan_t* out) {
-    (void)probe;
     if (!out || !build) return fail(EIGER_ERR_INVALID_ARG, "NULL build statistics or output");
     if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
     if (nb < 0 || np < 0 || nb > kMaxRows || np > kMaxRows)
         return fail(EIGER_ERR_INVALID_ARG, "row counts must be in [0, 2^32)");
     const bool nok = narrowable(dtype, nb, build->min, build->max);
-    *out = plan_rules(EIGER_AUTO, nb, np, dtype, nok, distinct_keys(build->estimate, nb), l2_bytes_or_default());
+    const double pd = probe && probe->n > 0 ? probe->estimate / (double)probe->n : -1.0;
+    *out = plan_rules(EIGER_AUTO, nb, np, dtype, nok, distinct_keys(build->estimate, nb), l2_bytes_or_default(),
+                      pd);
     if (dtype == EIGER_I32) out->narrow = 1;
     out->key_min = build->min;
     out->key_max = build->max;
@@ -976,8 +1016,7 @@ eiger_status eiger_groupby(eiger_dtype dtype, const void* d_keys, int64_t n, con
         EIGER_CUDA(cudaMemsetAsync(lay.ctrl, 0, sizeof(Ctrl), st), "control block reset");
         EIGER_CUDA(gb_run(GbArgs{d_keys, n, dtype}, pd, sc, ga, d_out_keys, (unsigned long long)capacity, lay.ctrl, st),
                    "group-by");
-        EIGER_CUDA(cudaMemcpyAsync(&h, lay.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "result readback");
-        EIGER_CUDA(cudaStreamSynchronize(st), "group-by synchronise");
+        EIGER_CUDA(readback_sync(&h, lay.ctrl, sizeof(Ctrl), st), "result readback");
         if (h.err & kErrInternal) return fail(EIGER_ERR_INTERNAL, "device consistency check failed");
         if (!(h.err & kErrTableFull)) break;
         // a table overflowed: enlarge the plan and run again

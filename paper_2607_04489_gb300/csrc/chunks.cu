@@ -145,13 +145,24 @@ __global__ void __launch_bounds__(256) chunk_fix_move_kernel(PairSink s, uint32_
         const uint32_t k0 = f.hb_pref[w], k1 = f.hb_pref[w + 1];
         if (k0 == k1) continue;
         const ChunkRec r = s.rec[w];
-        for (uint32_t k = k0 + lane; k < k1; k += kWarp) {
-            // the run holding the k-th filled position at or above C
-            uint32_t lo = 0, hi = nab;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (f.va_pref[mid] <= k) lo = mid; else hi = mid;
+        uint32_t run = 0;  // warp-uniform: the run holding filled position kb (below)
+        for (uint32_t kb = k0; kb < k1; kb += kWarp) {
+            // one binary search per 32 positions (lane 0), then each lane
+            // steps forward from there: 32 consecutive positions span at most
+            // a few runs, as a full run holds kOutChunk of them
+            if (lane == 0) {
+                uint32_t lo = run, hi = nab;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (f.va_pref[mid] <= kb) lo = mid; else hi = mid;
+                }
+                run = lo;
             }
+            run = __shfl_sync(0xffffffffu, run, 0);
+            const uint32_t k = kb + lane;
+            if (k >= k1) continue;
+            uint32_t lo = run;
+            while (lo + 1 < nab && f.va_pref[lo + 1] <= k) ++lo;
             const unsigned long long st = (c0 + lo) * kOutChunk;
             const unsigned long long src = (st > C ? st : C) + (k - f.va_pref[lo]);
             const unsigned long long dst = r.base + r.used + (k - k0);

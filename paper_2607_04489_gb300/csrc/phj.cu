@@ -251,6 +251,22 @@ __device__ __forceinline__ void load_round(RoundRegs<KeyT, N>& r, const KeyT* __
     }
 }
 
+// The 128-byte lines of rows [0, n) of a partitioned side (keys, then tuple
+// IDs unless rows are identified by position) asked into L2, one line per
+// participating thread and step (thread t of `threads`). A hint: no register
+// waits on it.
+template <bool POS, typename KeyT>
+__device__ __forceinline__ void prefetch_rows_l2(const KeyT* key, const uint32_t* idx, uint32_t n, uint32_t t,
+                                                 uint32_t threads) {
+    const uint32_t klines = (uint32_t)((n * sizeof(KeyT) + 127) / 128);
+    const uint32_t ilines = POS ? 0u : (n * 4u + 127) / 128;
+    for (uint32_t l = t; l < klines + ilines; l += threads) {
+        const char* p = l < klines ? reinterpret_cast<const char*>(key) + (size_t)l * 128
+                                   : reinterpret_cast<const char*>(idx) + (size_t)(l - klines) * 128;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+}
+
 constexpr uint32_t kHole = 0xFFFFFFFFu;  // stage position without a match
 
 // Warp-collective: the last partition p in [0, P) with prefix[p] <= item
@@ -446,11 +462,23 @@ __global__ void __launch_bounds__(kJoinThreads, (Rows<KeyT, PAIRS>::kMinBlocks))
                 s_next_item = claim;
                 s_next_part = pn2;
             }
+            // ask L2 for the start of the next partition's build rows and its
+            // first probe round, so that item starts on cache hits
+            if (claim < nitems) {
+                const uint32_t nb0 = a.bstart[pn2], nbn = min(a.bstart[pn2 + 1] - nb0, kBuildCap);
+                const uint32_t np0 = a.pstart[pn2], npn = min(a.pstart[pn2 + 1] - np0, kRound);
+                prefetch_rows_l2<POS>(a.bkey + nb0, a.bidx + nb0, nbn, threadIdx.x, kWarp);
+                prefetch_rows_l2<POS>(a.pkey + np0, a.pidx + np0, npn, threadIdx.x, kWarp);
+            }
         }
 
         for (uint32_t base = 0; base < pn; base += kRound) {
-            // the next round's loads are in flight while this round probes
+            // the next round's loads are in flight while this round probes,
+            // and the round after it is on its way into L2
             if (base + kRound < pn) load_round<POS>(nxt, pkey, pidx, base + kRound, pn, ppos0);
+            if (base + 2 * kRound < pn)
+                prefetch_rows_l2<POS>(pkey + base + 2 * kRound, pidx + base + 2 * kRound,
+                                      min(pn - (base + 2 * kRound), kRound), threadIdx.x, kJoinThreads);
             if (unique) {
                 // Fast path: stop at the first match, no collectives per step.
 #pragma unroll

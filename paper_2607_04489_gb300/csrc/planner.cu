@@ -23,7 +23,18 @@
 //    2^28 x 2^30: 31.1 against 34.8 ms): they keep the second pass at 256
 //    digits where 2048-3072-row partitions need 512, whose 8-row digit runs
 //    and doubled count arrays slow that pass by a third; below 2^27 they lose
-//    (2^24: 1.81 against 1.72 ms).
+//    (2^24: 1.81 against 1.72 ms);
+//  - except under heavy probe skew: when a probe sample of 2^20 rows holds
+//    fewer than kSkewHeavy distinct keys per row (Zipf theta ~1.5 gives
+//    0.014), or fewer than kSkewModerate with the NPHJ table within 4x the
+//    L2 cache (theta ~1 gives 0.22-0.45), and the probe side is at least
+//    twice the build side, 32-bit keys go to the NPHJ: hot keys keep their
+//    slots in cache, while the partitioned join funnels them through one
+//    partition. Measured on the GB300 variant-sweep grid (ms, NPHJ against
+//    the rules' PHJ): 2^24 x 4, theta 1.5: 1.40 / 1.90; 2^24 x 16, theta 1:
+//    3.73 / 5.13; 2^26 x 16, theta 1.5: 12.95 / 25.1; 2^28 x 4, theta 1.5:
+//    28.4 / 33.5; without skew the PHJ wins (2^28 x 4: 49.6 / 31.1). With
+//    16-byte slots (64-bit keys) the skewed NPHJ loses from 2^26 up.
 #include <algorithm>
 #include <cmath>
 
@@ -40,6 +51,8 @@ constexpr int64_t kLargeBuild = 1ll << 27;
 static_assert(kTargetRowsDistinctLarge < EIGER_BUILD_CAP, "an average partition fits one table");
 constexpr double kDistinctFraction = 0.9;  // estimate / rows above which the keys count as distinct
 constexpr int kOnePassBits = 8;
+constexpr double kSkewHeavy = 0.1;     // probe sample distinct fraction: heavy skew
+constexpr double kSkewModerate = 0.5;  // ... moderate skew
 constexpr int kMaxTotalBits = 20;
 }  // namespace
 
@@ -64,9 +77,13 @@ unsigned long long table_slots(int64_t nb, double load_factor) {
     return s;
 }
 
+bool wants_probe_sample(const eiger_plan_t& rules_plan, int64_t nb, int64_t np, int dtype, bool narrowable) {
+    const bool key32 = dtype == EIGER_I32 || narrowable;
+    return key32 && np >= 2 * nb && (rules_plan.variant == EIGER_PHJ1 || rules_plan.variant == EIGER_PHJ2);
+}
+
 eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool narrowable, bool distinct,
-                        size_t l2_bytes) {
-    (void)np;
+                        size_t l2_bytes, double probe_distinct) {
     eiger_plan_t p{};
     p.selector = 0;
     p.load_factor = 0.5f;
@@ -76,7 +93,10 @@ eiger_plan_t plan_rules(int variant, int64_t nb, int64_t np, int dtype, bool nar
     int v = variant;
     if (v == EIGER_AUTO) {
         const unsigned long long bytes = table_slots(nb, 0.5) * (key32 ? 8ull : 16ull);
-        if (bytes <= l2_bytes / 2)
+        const bool skewed = key32 && np >= 2 * nb && probe_distinct >= 0.0 &&
+                            (probe_distinct < kSkewHeavy ||
+                             (probe_distinct < kSkewModerate && bytes <= 4ull * l2_bytes));
+        if (bytes <= l2_bytes / 2 || skewed)
             v = EIGER_NPHJ;
         else
             v = B <= kOnePassBits ? EIGER_PHJ1 : EIGER_PHJ2;

@@ -128,9 +128,21 @@ __global__ void __launch_bounds__(256)
                        int grid, StatsDev* __restrict__ out) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w < kHllM / 4) {
-        uint32_t m = 0;
-        for (int g = 0; g < grid; ++g) m = __vmaxu4(m, part_regs[(size_t)g * (kHllM / 4) + w]);
-        out->regs[w] = m;
+        // four independent running maxima, so 16 loads are in flight per
+        // thread instead of one dependent load per partial array
+        uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+        const uint32_t* p = part_regs + w;
+        constexpr size_t W = kHllM / 4;
+        int g = 0;
+#pragma unroll 4
+        for (; g + 4 <= grid; g += 4) {
+            m0 = __vmaxu4(m0, p[(size_t)(g + 0) * W]);
+            m1 = __vmaxu4(m1, p[(size_t)(g + 1) * W]);
+            m2 = __vmaxu4(m2, p[(size_t)(g + 2) * W]);
+            m3 = __vmaxu4(m3, p[(size_t)(g + 3) * W]);
+        }
+        for (; g < grid; ++g) m0 = __vmaxu4(m0, p[(size_t)g * W]);
+        out->regs[w] = __vmaxu4(__vmaxu4(m0, m1), __vmaxu4(m2, m3));
     }
     if (blockIdx.x == 0) {
         __shared__ int64_t s_mn[256 / kWarp], s_mx[256 / kWarp];

@@ -53,19 +53,29 @@ class JoinSpec:
     span_log2: float
     distinct_frac: float
     theta: float
+    unique: bool = False  # build keys are distinct (each of the ndv = nb values once)
 
 
-def draw_spec(seed: int, log2_lo: float = 10.0, log2_hi: float = 24.0) -> JoinSpec:
-    """Build 2^U(lo, hi) rows, probe ratio U(1, 16), key width 4 or 8 bytes,
-    key span 2^U(16, 63) clamped to the width, distinct fraction U(0.01, 1),
-    probe skew theta U(0, 1.5)."""
+def draw_spec(seed: int, log2_lo: float = 10.0, log2_hi: float = 24.0, large_hi: float = 27.0,
+              p_large: float = 0.1, p_unique: float = 0.25) -> JoinSpec:
+    """Build 2^U(lo, hi) rows (one join in ten: 2^U(hi, large_hi)), probe
+    ratio U(1, 16), key width 4 or 8 bytes, key span 2^U(16, 63) clamped to
+    the width, probe skew theta U(0, 1.5). One join in four has unique build
+    keys (span at least twice the rows); the others draw their build rows from
+    a distinct fraction U(0.01, 1) of nb values, with repetition."""
     r = np.random.default_rng(seed)
-    nb = int(2 ** r.uniform(log2_lo, log2_hi))
+    large = r.uniform() < p_large
+    nb = int(2 ** (r.uniform(log2_hi, large_hi) if large else r.uniform(log2_lo, log2_hi)))
     np_ = min(int(nb * r.uniform(1, 16)), (1 << 32) - 1)
     kb = int(r.choice([4, 8]))
     span_log2 = min(float(r.uniform(16, 63)), 32.0 if kb == 4 else 63.0)
-    return JoinSpec(seed, max(nb, 1), max(np_, 1), kb, span_log2, float(r.uniform(0.01, 1.0)),
-                    float(r.uniform(0.0, 1.5)))
+    unique = bool(r.uniform() < p_unique)
+    frac = float(r.uniform(0.01, 1.0))
+    theta = float(r.uniform(0.0, 1.5))
+    if unique:
+        frac = 1.0
+        span_log2 = min(max(span_log2, math.log2(max(nb, 2)) + 1.0), 32.0 if kb == 4 else 63.0)
+    return JoinSpec(seed, max(nb, 1), max(np_, 1), kb, span_log2, frac, theta, unique)
 
 
 def make_join(spec: JoinSpec, device="cuda"):
@@ -87,7 +97,10 @@ def make_join(spec: JoinSpec, device="cuda"):
             draw = torch.randint(lo, hi, (want,), generator=g, device=device, dtype=torch.int64)
             vals = torch.unique(torch.cat([vals, draw]))
         vals = vals[torch.randperm(vals.numel(), generator=g, device=device)[:ndv]]
-    bk = vals[torch.randint(0, ndv, (spec.nb,), generator=g, device=device)].to(dt)
+    if spec.unique and ndv == spec.nb:
+        bk = vals.to(dt)  # every value once, in random order
+    else:
+        bk = vals[torch.randint(0, ndv, (spec.nb,), generator=g, device=device)].to(dt)
     rank = workloads.zipf_ranks(ndv, spec.theta, spec.np, spec.seed * 7919 + 2, device)
     order = torch.randperm(ndv, generator=g, device=device)
     pk = vals[order[rank]].to(dt)

@@ -88,6 +88,30 @@ def test_planner_distinct_build_keys_get_larger_partitions(lib):
     assert (big_u.bits1, big_u.bits2) == (8, 8) and (big_d.bits1, big_d.bits2) == (8, 9)
 
 
+def test_planner_skewed_probe_sample_prefers_the_non_partitioned_join(lib):
+    """A probe sample with few distinct keys per row (heavy skew) sends 32-bit
+    keys with np >= 2 nb to the NPHJ; moderate skew only while its table is
+    within 4x the L2 cache; no sample, a ratio below 2 or 64-bit keys keep
+    the partitioned plan."""
+    s = 1 << 20
+
+    def plan(log2nb, ratio, frac, lo=0, width=None):
+        nb = 1 << log2nb
+        hi = lo + (width if width is not None else nb - 1)
+        b = _stats(nb, lo, hi)
+        p = _stats(s, lo, hi, est=frac * s) if frac is not None else None
+        return lib.plan(b, p, nb, ratio * nb, lib.I64).variant
+
+    assert plan(26, 4, 0.014) == "nphj"            # Zipf 1.5-like
+    assert plan(28, 4, 0.014) == "nphj"
+    assert plan(24, 4, 0.35) == "nphj"             # Zipf 1-like, table 256 MB
+    assert plan(26, 4, 0.35) == "phj2"             # ... table 1 GB
+    assert plan(26, 4, 0.98) == "phj2"             # uniform
+    assert plan(26, 4, None) == "phj2"             # not profiled
+    assert plan(26, 1, 0.014) == "phj2"            # ratio below 2
+    assert plan(26, 4, 0.014, lo=-2**62, width=2**63) == "phj2"  # 64-bit keys (16-byte slots)
+
+
 def _target(nb, distinct):
     return (4096 if nb >= 1 << 27 else 3072) if distinct else 2048
 

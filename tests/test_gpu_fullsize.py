@@ -50,10 +50,12 @@ def _check_unique_build_result(w, r):
     assert bool((w.build_keys[b] == w.probe_keys[p]).all())
 
 
-@pytest.mark.parametrize("keys,theta", [("dense", 0.0), ("random", 0.0), ("dense", 1.5)])
-def test_largest_sweep_join(eiger, keys, theta):
+@pytest.mark.parametrize("keys,theta,variant", [("dense", 0.0, "phj2"), ("random", 0.0, "phj2"),
+                                                 ("dense", 1.5, "nphj")])
+def test_largest_sweep_join(eiger, keys, theta, variant):
     """AUTO at nb = 2^28, np = 2^30 (the benchmark's default call for dense
-    uniform keys)."""
+    uniform keys); with Zipf 1.5 probes the probe sample sends it to the
+    non-partitioned join."""
     from paper_2607_04489_gb300 import workloads
 
     _need(110)
@@ -61,8 +63,23 @@ def test_largest_sweep_join(eiger, keys, theta):
     w.build_pay = w.probe_pay = None
     torch.cuda.empty_cache()
     r = eiger.join(w.build_keys, w.probe_keys, variant="auto")
-    assert r.plan.variant == "phj2"
+    assert r.plan.variant == variant
     assert r.plan.narrow == (1 if keys == "dense" else 0)
+    _check_unique_build_result(w, r)
+
+
+def test_largest_sweep_join_skewed_partitioned(eiger):
+    """The partitioned join forced on the Zipf 1.5 probes at 2^28 x 2^30: one
+    key takes ~38 % of the probe rows, so its partition's probe side is cut
+    into thousands of chunks over one build table."""
+    from paper_2607_04489_gb300 import workloads
+
+    _need(110)
+    w = workloads.variant_sweep(1 << 28, 4, keys="dense", theta=1.5, seed=0, device="cuda", payload_bytes=8)
+    w.build_pay = w.probe_pay = None
+    torch.cuda.empty_cache()
+    r = eiger.join(w.build_keys, w.probe_keys, variant="phj2", knobs=eiger.Plan("phj2", 8, 8, 1))
+    assert (r.plan.variant, r.plan.bits1, r.plan.bits2) == ("phj2", 8, 8)
     _check_unique_build_result(w, r)
 
 
