@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.0)
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--copy-streams", type=int, default=4,
+                    help="end to end: each host<->device copy is split over this many streams per direction")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-static", action="store_true")
     ap.add_argument("--selectivity", type=float, default=1.0, help="star workload: fact rows kept")
@@ -415,39 +417,48 @@ def run_eiger(args):
         dpk = [pk, torch.empty_like(pk)]
         dob = [out_b, torch.empty_like(out_b)]
         dop = [out_p, torch.empty_like(out_p)]
-        h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        up_done = [torch.cuda.Event() for _ in range(2)]
+        # each direction's copies are split into --copy-streams chunks on as
+        # many streams, so several copy engines run at once
+        cs = max(1, args.copy_streams)
+        h2ds = [torch.cuda.Stream(dev) for _ in range(cs)]
+        d2hs = [torch.cuda.Stream(dev) for _ in range(cs)]
+        h2d, d2h = h2ds[0], d2hs[0]
+        up_done = [[torch.cuda.Event() for _ in range(cs)] for _ in range(2)]
         join_done = [torch.cuda.Event() for _ in range(2)]
-        down_done = [torch.cuda.Event() for _ in range(2)]
+        down_done = [[torch.cuda.Event() for _ in range(cs)] for _ in range(2)]
+
+        def split_copy(streams, done, pairs, after):
+            for q, s_ in enumerate(streams):
+                s_.wait_event(after)
+                with torch.cuda.stream(s_):
+                    for dst, src in pairs:
+                        dst.chunk(cs)[q].copy_(src.chunk(cs)[q], non_blocking=True)
+                done[q].record(s_)
 
         def upload(slot):
-            h2d.wait_event(join_done[slot])  # the join that last read this slot is done
-            with torch.cuda.stream(h2d):
-                dbk[slot].copy_(hb, non_blocking=True)
-                dpk[slot].copy_(hp, non_blocking=True)
-            up_done[slot].record(h2d)
+            # after the join that last read this slot
+            split_copy(h2ds, up_done[slot], [(dbk[slot], hb), (dpk[slot], hp)], join_done[slot])
 
         def run_steps(n):
             for q in range(2):
                 join_done[q].record(stream)
-                down_done[q].record(stream)
+                for ev in down_done[q]:
+                    ev.record(stream)
             upload(0)
             for i in range(n):
                 slot = i & 1
                 if i + 1 < n:
                     upload(slot ^ 1)
-                stream.wait_event(up_done[slot])
-                stream.wait_event(down_done[slot])  # its output arrays were copied out
+                for ev in up_done[slot]:
+                    stream.wait_event(ev)
+                for ev in down_done[slot]:
+                    stream.wait_event(ev)  # its output arrays were copied out
                 st, cnt, _ = eiger.join_into(dbk[slot], dpk[slot], variant=args.variant, out_bidx=dob[slot],
                                              out_pidx=dop[slot], capacity=np_, workspace=ws, stream=stream)
                 if st != eiger.OK or cnt != np_:
                     raise RuntimeError(f"join failed: {eiger.last_error()}")
                 join_done[slot].record(stream)
-                d2h.wait_event(join_done[slot])
-                with torch.cuda.stream(d2h):
-                    hob.copy_(dob[slot], non_blocking=True)
-                    hop.copy_(dop[slot], non_blocking=True)
-                down_done[slot].record(d2h)
+                split_copy(d2hs, down_done[slot], [(hob, dob[slot]), (hop, dop[slot])], join_done[slot])
 
         run_steps(max(2, args.warmup))
         torch.cuda.synchronize(dev)
@@ -455,9 +466,12 @@ def run_eiger(args):
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(h2d)
+        for s_ in h2ds[1:] + d2hs + [stream]:
+            s_.wait_stream(h2d)  # nothing of the timed steps starts before t0
         run_steps(args.steps)
         for q in range(2):
-            d2h.wait_event(down_done[q])
+            for ev in down_done[q]:
+                d2h.wait_event(ev)
             d2h.wait_event(join_done[q])
         t1.record(d2h)
         torch.cuda.synchronize(dev)
@@ -468,6 +482,7 @@ def run_eiger(args):
                "d2h_bytes_per_step": int(2 * 4 * np_),
                "through": "torch copies from/to pinned host memory around the device-pointer C-ABI call "
                           "eiger_join (the ABI takes device pointers)",
+               "copy_streams_per_direction": cs,
                "pipelining": "upload of step i+1 and download of step i-1 overlap the join of step i"}
         del dbk[1], dpk[1], dob[1], dop[1], hb, hp, hob, hop
 
@@ -576,10 +591,28 @@ def run_batched(args):
                        "joins": args.batch_joins, "tuples": tuples,
                        "knobs": vars(bj.knobs) if hasattr(bj.knobs, "__dict__") else str(bj.knobs)},
             "sequential_static": sequential,
+            "roofline": batch_roofline(w, ms),
             "gpu_launches": 4 * args.steps, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
     return 0
+
+
+def batch_roofline(w, ms):
+    """Compulsory bytes of one replay of the batch (every 4-byte build and
+    probe key read once, one 8-byte pair written per match; every probe row of
+    this workload matches once) over the whole replay's time, which also holds
+    the batch's three small launches: a lower bound on batch_join's own
+    bandwidth."""
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    nb = sum(int(b.numel()) for b in w.builds)
+    np_ = sum(int(p.numel()) for p in w.probes)
+    by = 4.0 * (nb + np_) + 8.0 * np_
+    gbs = by / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "batch_join", "achieved": gbs, "peak": hbm, "peak_source": src,
+            "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "algorithmic_bytes": by,
+            "timing": "CUDA events around whole graph replays (batch_join plus three small launches)"}
 
 
 def stage_table(stages):

@@ -19,7 +19,10 @@
  *    never allocates, frees or retains them beyond the call.
  *  - Scratch memory ("workspace") is supplied by the caller; its size comes
  *    from the matching *_workspace query. Contents need not be initialised and
- *    are garbage after the call.
+ *    are garbage after the call. The library allocates no device memory; it
+ *    keeps one 32 KB page-locked host buffer per calling host thread, made on
+ *    first use, for reading small results back (eiger_join_static_noalloc
+ *    uses none).
  *  - `stream` is a CUDA stream handle (cudaStream_t / CUstream) passed as
  *    void*; NULL means the legacy default stream. Work is enqueued on it.
  *    Calls that return host-side results (statistics, match counts)
