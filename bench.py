@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.0)
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--copy-streams", type=int, default=4,
+    ap.add_argument("--copy-streams", type=int, default=1,
                     help="end to end: each host<->device copy is split over this many streams per direction")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-static", action="store_true")
@@ -105,38 +105,48 @@ def barrier(world: int):
         dist.barrier()
 
 
-def kernel_sources_digest() -> str:
-    """Digest of the CUDA sources, to tell whether recorded ncu counters still
-    describe the kernels that run."""
-    import glob
+# Source files that define each timed kernel (its own translation unit and the
+# headers it includes); recorded ncu counters stay valid while these hash the same.
+KERNEL_SOURCES = {
+    "phj_join": ("phj.cu", "chunks.cuh", "emit.cuh", "common.cuh", "kernels.cuh"),
+    "part_scatter": ("partition.cu", "common.cuh", "kernels.cuh"),
+    "part_hist": ("partition.cu", "common.cuh", "kernels.cuh"),
+}
+
+
+def kernel_sources_digest(kernel: str) -> str | None:
+    """Digest of the CUDA sources that define `kernel` (a stage name such as
+    "phj_join" or "part_scatter.p1.probe"), to tell whether recorded ncu
+    counters still describe the kernel that runs; None for an unlisted one."""
     import hashlib
 
+    files = KERNEL_SOURCES.get(kernel.split(".")[0])
+    if not files:
+        return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2607_04489_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
-                   glob.glob(os.path.join(csrc, "*.h")))
-    for p in files:
-        h.update(os.path.basename(p).encode())
-        with open(p, "rb") as f:
+    for name in files:
+        h.update(name.encode())
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str = "sweep"):
+def recorded_traffic(kernel: str, workload: str | None):
     """DRAM bytes per launch of `kernel` in `workload` from
-    profiles/dram_traffic.txt, or None when the file is missing, has no such
-    entry, or was taken on other kernel sources."""
+    profiles/dram_traffic.txt (lines: workload kernel bytes sources-digest),
+    or None when there is no such entry or the kernel's sources changed since
+    the counters were taken."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         with open(path) as f:
             rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
     except OSError:
         return None
-    digest = next((r[1] for r in rows if len(r) == 2 and r[0] == "sources"), None)
-    table = {(r[0], r[1]): r[2] for r in rows if len(r) == 3}
-    if digest != kernel_sources_digest() or (workload, kernel) not in table:
-        return None
-    return float(table[(workload, kernel)])
+    for r in rows:
+        if len(r) == 4 and (r[0], r[1]) == (workload, kernel) and r[3] == kernel_sources_digest(kernel):
+            return float(r[2])
+    return None
 
 
 def measured_peaks():
@@ -325,6 +335,11 @@ def run_eiger(args):
                                 device=dev, payload_bytes=8)
     w.build_pay = w.probe_pay = None
     torch.cuda.empty_cache()
+    # Everything below runs on one created (non-blocking) stream rather than
+    # the legacy default stream, whose implicit synchronisation would tie the
+    # joins to the end-to-end copies' streams.
+    torch.cuda.synchronize(dev)
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
     bk, pk = w.build_keys, w.probe_keys
     out_b = torch.empty(np_, dtype=torch.int32, device=dev)
     out_p = torch.empty(np_, dtype=torch.int32, device=dev)
@@ -489,7 +504,7 @@ def run_eiger(args):
     # ---- roofline of the dominant stage (from the profiling pass)
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    stage_rows = stage_table(stages)
+    stage_rows = stage_table(stages, max(1, args.profile_steps))
     dom = stage_rows[0] if stage_rows else {"stage": None, "gbs": 0.0, "bytes": 0.0}
     compulsory = nb * 8 + np_ * 8 + np_ * 8  # keys in, pairs out
     line = {
@@ -615,10 +630,35 @@ def batch_roofline(w, ms):
             "timing": "CUDA events around whole graph replays (batch_join plus three small launches)"}
 
 
-def stage_table(stages):
+def profile_pass(step, steps):
+    """Per-launch CUDA-event stage times of `steps` more calls of `step`,
+    after the timed region (which runs without the events): name ->
+    [ms, bytes, entries] summed over the steps, and the launches."""
+    from paper_2607_04489_gb300 import eiger
+
+    stages, launches = {}, 0
+    eiger.profile(True)
+    try:
+        for _ in range(steps):
+            step()
+            for name, ms, nl, by in eiger.profile_read():
+                st_ = stages.setdefault(name, [0.0, 0.0, 0])
+                st_[0] += ms
+                st_[1] += by
+                st_[2] += 1
+                launches += nl
+    finally:
+        eiger.profile(False)
+    return stages, launches
+
+
+def stage_table(stages, steps):
+    """Per-step device time and algorithmic bytes of each named stage (a name
+    that occurs several times in a step, like the statistics of the build side
+    and of a probe sample, adds up), sorted by time."""
     rows = []
     for name, (ms_tot, by_tot, cnt) in stages.items():
-        ms_avg, by_avg = ms_tot / cnt, by_tot / cnt
+        ms_avg, by_avg = ms_tot / steps, by_tot / steps
         rows.append({"stage": name, "ms": round(ms_avg, 4), "bytes": by_avg,
                      "gbs": by_avg / (ms_avg * 1e-3) / 1e9 if ms_avg > 0 else None})
     rows.sort(key=lambda r: -r["ms"])
@@ -774,27 +814,16 @@ def run_wide(args):
 
         for _ in range(args.warmup):
             plan = step()
-        stages, launches = {}, 0
-        if profile:
-            eiger.profile(True)
         barrier(world)
         torch.cuda.synchronize(dev)
         e0.record(stream)
         for _ in range(args.steps):
             plan = step()
-            if profile:
-                for name, ms, nl, by in eiger.profile_read():
-                    st_ = stages.setdefault(name, [0.0, 0.0, 0])
-                    st_[0] += ms
-                    st_[1] += by
-                    st_[2] += 1
-                    launches += nl
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
-        if profile:
-            eiger.profile(False)
         ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        stages, launches = profile_pass(step, args.steps) if profile else ({}, 0)
         del ws
         torch.cuda.empty_cache()
         return ms, plan, stages, launches
@@ -815,7 +844,7 @@ def run_wide(args):
                       "plan": f"{aplan.variant}/{aplan.bits1}/{aplan.bits2}/{aplan.materialize}"}
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    rows = stage_table(stages)
+    rows = stage_table(stages, args.steps)
     dom = rows[0]
     line = {"metric": METRIC, "value": tuples / (ms * 1e-3), "unit": "tuples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -880,27 +909,16 @@ def run_groupby(args):
 
         for _ in range(args.warmup):
             plan, cnt = step()
-        stages, launches = {}, 0
-        if profile:
-            eiger.profile(True)
         barrier(world)
         torch.cuda.synchronize(dev)
         e0.record(stream)
         for _ in range(args.steps):
             plan, cnt = step()
-            if profile:
-                for name, ms, nl, by in eiger.profile_read():
-                    st_ = stages.setdefault(name, [0.0, 0.0, 0])
-                    st_[0] += ms
-                    st_[1] += by
-                    st_[2] += 1
-                    launches += nl
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
-        if profile:
-            eiger.profile(False)
         ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        stages, launches = profile_pass(step, args.steps) if profile else ({}, 0)
         del ws
         torch.cuda.empty_cache()
         return ms, plan, cnt, stages, launches
@@ -918,7 +936,7 @@ def run_groupby(args):
                    "plan": f"{aplan.variant}/{aplan.bits1}/{aplan.bits2}/{aplan.table_slots}"}
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    rows = stage_table(stages)
+    rows = stage_table(stages, args.steps)
     dom = rows[0]
     line = {"metric": "group-by rows/s: HLL-guided choice vs hash and partition", "value": tuples / (ms * 1e-3),
             "unit": "rows/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -971,28 +989,20 @@ def run_star(args):
         for _ in range(args.warmup):
             res = eiger.join_sum(w.build_keys, w.build_pay, w.probe_keys, w.probe_pay, variant=variant,
                                  materialize=mat, workspace=ws, stream=stream)
-        stages, launches = {}, 0
-        if profile:
-            eiger.profile(True)
+        def step():
+            return eiger.join_sum(w.build_keys, w.build_pay, w.probe_keys, w.probe_pay, variant=variant,
+                                  materialize=mat, workspace=ws, stream=stream)
+
         barrier(world)
         torch.cuda.synchronize(dev)
         e0.record(stream)
         for _ in range(args.steps):
-            res = eiger.join_sum(w.build_keys, w.build_pay, w.probe_keys, w.probe_pay, variant=variant,
-                                 materialize=mat, workspace=ws, stream=stream)
-            if profile:
-                for name, ms, nl, by in eiger.profile_read():
-                    st_ = stages.setdefault(name, [0.0, 0.0, 0])
-                    st_[0] += ms
-                    st_[1] += by
-                    st_[2] += 1
-                    launches += nl
+            res = step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
-        if profile:
-            eiger.profile(False)
         ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        stages, launches = profile_pass(step, args.steps) if profile else ({}, 0)
         del ws
         torch.cuda.empty_cache()
         return ms, res, stages, launches
@@ -1009,7 +1019,7 @@ def run_star(args):
         raise RuntimeError("gathered and carried sums differ")
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    rows = stage_table(stages)
+    rows = stage_table(stages, args.steps)
     dom = rows[0]
     line = {"metric": METRIC, "value": tuples / (ms * 1e-3), "unit": "tuples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

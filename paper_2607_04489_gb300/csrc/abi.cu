@@ -53,11 +53,13 @@ struct SideStreams {
 };
 thread_local SideStreams g_side;
 
-// Page-locked host staging for the small results a call reads back (the
-// statistics, the control block): a copy into pageable memory goes through a
-// driver staging buffer and costs a few microseconds more per call. One
-// buffer per host thread, allocated on first use and kept until exit; on
-// failure the caller's pageable destination is used directly.
+// Page-locked, device-mapped host staging for the small results a call reads
+// back (the statistics, the control block). A kernel stores them straight
+// into host memory, so the readback never waits in a copy engine's queue
+// behind the caller's bulk transfers (a 16 KB copy queued behind a multi-GB
+// download of a previous batch's pairs waits for all of it). One buffer per
+// host thread, allocated on first use and kept until exit; when it cannot be
+// had, the result is copied into the caller's destination by cudaMemcpyAsync.
 constexpr size_t kStageBytes = 32 << 10;
 thread_local void* g_host_stage = nullptr;
 thread_local bool g_host_stage_failed = false;
@@ -65,7 +67,7 @@ thread_local bool g_host_stage_failed = false;
 void* host_stage(size_t bytes) {
     if (bytes > kStageBytes || g_host_stage_failed) return nullptr;
     if (!g_host_stage) {
-        if (cudaHostAlloc(&g_host_stage, kStageBytes, cudaHostAllocPortable) != cudaSuccess) {
+        if (cudaHostAlloc(&g_host_stage, kStageBytes, cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess) {
             cudaGetLastError();
             g_host_stage = nullptr;
             g_host_stage_failed = true;
@@ -74,15 +76,34 @@ void* host_stage(size_t bytes) {
     return g_host_stage;
 }
 
+// One CTA stores `words` 32-bit words of device memory into mapped host memory.
+__global__ void __launch_bounds__(256) store_to_host_kernel(uint32_t* __restrict__ dst,
+                                                            const uint32_t* __restrict__ src, uint32_t words) {
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
 }  // namespace
 
-// Device-to-host copy of a small result on `stream`, then a synchronisation
-// of the stream; through the page-locked staging buffer when it exists.
+// Small result from device memory to `dst` on `stream`, then a synchronisation
+// of the stream: stored by a kernel into the mapped staging buffer when it
+// exists (bytes a multiple of 4), else copied by cudaMemcpyAsync.
 cudaError_t readback_sync(void* dst, const void* src, size_t bytes, cudaStream_t stream) {
-    void* st = host_stage(bytes);
-    cudaError_t e = cudaMemcpyAsync(st ? st : dst, src, bytes, cudaMemcpyDeviceToHost, stream);
+    void* st = bytes % 4 == 0 ? host_stage(bytes) : nullptr;
+    void* st_dev = nullptr;
+    if (st && cudaHostGetDevicePointer(&st_dev, st, 0) != cudaSuccess) {
+        cudaGetLastError();
+        st_dev = nullptr;
+    }
+    cudaError_t e;
+    if (st_dev) {
+        store_to_host_kernel<<<1, 256, 0, stream>>>(static_cast<uint32_t*>(st_dev), static_cast<const uint32_t*>(src),
+                                                   (uint32_t)(bytes / 4));
+        e = cudaGetLastError();
+    } else {
+        e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e == cudaSuccess && st) std::memcpy(dst, st, bytes);
+    if (e == cudaSuccess && st_dev) std::memcpy(dst, st, bytes);
     return e;
 }
 

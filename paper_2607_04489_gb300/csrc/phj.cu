@@ -363,7 +363,11 @@ template <typename KeyT, bool AGG, bool PAIRS, bool POS>
 __global__ void __launch_bounds__(kJoinThreads, (Rows<KeyT, PAIRS>::kMinBlocks))
     phj_join_kernel(JoinIn<KeyT> a, JoinOut out, PairSink sink, Ctrl* ctrl) {
     extern __shared__ __align__(16) unsigned char smem[];
-    // the stage follows the table in dynamic shared memory (none with PAIRS)
+    // the stage follows the table in dynamic shared memory; index pairs and
+    // aggregates use none, so none is allocated for them (shared memory left
+    // unreserved serves as L1 cache, which the payload gathers of the
+    // aggregate need)
+    constexpr bool kStage = !PAIRS && !AGG;
     Stage<kJoinStage>& st = *reinterpret_cast<Stage<kJoinStage>*>(smem + (size_t)kTableMax * SmemTable<KeyT>::kSlotBytes);
     __shared__ uint32_t s_grp[kMaxRows * kJoinWarps];
     __shared__ unsigned long long s_next_item;
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(kJoinThreads, (Rows<KeyT, PAIRS>::kMinBlocks))
     constexpr uint32_t kRound = Rows<KeyT, PAIRS>::kRound;
     SmemTable<KeyT> tab;
     tab.bind(smem);
-    if (!PAIRS && threadIdx.x == 0) st.count = 0;
+    if (kStage && threadIdx.x == 0) st.count = 0;
     AggState agg{0ull, 0ull};
     WarpChunk wc;
     wc.init();
@@ -569,8 +573,8 @@ __global__ void __launch_bounds__(kJoinThreads, (Rows<KeyT, PAIRS>::kMinBlocks))
 }
 
 template <typename KeyT>
-size_t join_smem(bool pairs) {
-    return (size_t)kTableMax * SmemTable<KeyT>::kSlotBytes + (pairs ? 0 : sizeof(Stage<kJoinStage>));
+size_t join_smem(bool stage) {
+    return (size_t)kTableMax * SmemTable<KeyT>::kSlotBytes + (stage ? sizeof(Stage<kJoinStage>) : 0);
 }
 
 template <typename KeyT>
@@ -603,7 +607,7 @@ cudaError_t launch_join(const PhjScratch& s, const PlanDev& plan, const JoinOut&
                  pos_agg ? (double)sizeof(KeyT) * (double)(nb + np) + (double)out.b.bytes[0] * (double)nb
                          : tuple * (double)(nb + np),
                  stream, pos_agg ? (double)out.p.bytes[0] : match_bytes(out));
-    const size_t smem = join_smem<KeyT>(pairs);
+    const size_t smem = join_smem<KeyT>(!pairs && !out.aggregate);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
