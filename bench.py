@@ -64,12 +64,14 @@ def parse():
     ap.add_argument("--selectivity", type=float, default=1.0, help="star workload: fact rows kept")
     ap.add_argument("--grid-sizes", default="20,22,24,26,28", help="grid workload: log2 build sizes")
     ap.add_argument("--grid-reps", type=int, default=3, help="grid workload: timed runs per plan")
-    ap.add_argument("--workload", choices=["sweep", "batched", "wide", "groupby", "star", "grid"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "batched", "wide", "groupby", "star", "grid", "small"],
+                    default="sweep",
                     help="sweep: the headline join; batched: 4096 small joins in one launch; "
                          "wide: four columns per relation, the payloads materialised; "
                          "groupby: 2^28 rows, two aggregations, 2^--groups-log2 groups; "
                          "star: the 150M x 600M foreign-key join with the exact payload sum; "
-                         "grid: the variant-sweep grid, every plan timed at every point (one JSON line each)")
+                         "grid: the variant-sweep grid, every plan timed at every point (one JSON line each); "
+                         "small: the 1M x 4M int32 static-join workload with the probe statistics")
     ap.add_argument("--groups-log2", type=int, default=20, help="groupby workload: log2 of the group count")
     ap.add_argument("--log2-rows", type=int, default=28, help="groupby workload: log2 of the rows")
     ap.add_argument("--key-bytes", type=int, choices=[4, 8], default=4, help="wide workload key/payload width")
@@ -665,6 +667,79 @@ def stage_table(stages, steps):
     return rows
 
 
+def run_small(args):
+    """The small static-join workload: 2^20 unique int32 build keys (a
+    permutation), 2^22 uniform probe keys over them (every probe row matches
+    once), and eiger_stats on the probe keys. AUTO and the static join are
+    timed per call; the CPU oracle runs the same full join (canonical pair
+    sort included) on all host cores and on one."""
+    import torch
+
+    from paper_2607_04489_gb300 import eiger, workloads
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    eiger.load()
+    wc = workloads.small_static(1 << 20, 1 << 22, device="cpu")
+    bk, pk = wc.build_keys.to(dev), wc.probe_keys.to(dev)
+    nb, np_ = bk.numel(), pk.numel()
+    ob = torch.empty(np_, dtype=torch.int32, device=dev)
+    op = torch.empty_like(ob)
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / args.steps
+
+    arms = {}
+    for variant in ("auto", "static"):
+        ws = torch.empty(eiger.join_workspace(nb, np_, eiger.I32, variant), dtype=torch.uint8, device=dev)
+        holder = {}
+
+        def call():
+            st, cnt, plan = eiger.join_into(bk, pk, variant=variant, out_bidx=ob, out_pidx=op, capacity=np_,
+                                            workspace=ws, stream=stream)
+            if st != eiger.OK or cnt != np_:
+                raise RuntimeError(f"join failed: {eiger.last_error()}")
+            holder["plan"] = plan
+
+        ms = timed(call)
+        arms[variant] = {"ms_per_step": ms, "value": (nb + np_) / (ms * 1e-3), "unit": "tuples/s",
+                         "plan": f"{holder['plan'].variant} {holder['plan'].bits1}+{holder['plan'].bits2}"}
+    sws = torch.empty(eiger.stats_workspace(np_, eiger.I32), dtype=torch.uint8, device=dev)
+    sms = timed(lambda: eiger.stats(pk, workspace=sws, stream=stream))
+    import oracle
+
+    b, p = wc.build_keys.numpy(), wc.probe_keys.numpy()
+    cores = host_cores()
+    tn, rn, en = _oracle_leg(b, p, cores, 3.0, max_runs=8)
+    t1, r1, e1_ = _oracle_leg(b, p, 1, 3.0, max_runs=8)
+    ms = arms["auto"]["ms_per_step"]
+    line = {"metric": METRIC, "value": arms["auto"]["value"], "unit": "tuples/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "small static join: 2^20 unique int32 build keys (permutation), 2^22 "
+                                   "uniform probe keys over them; eiger_stats on the probe keys",
+                       "l2": "inputs (20 MB) fit L2: the 60 % HBM target does not apply"},
+            "arms": arms, "static_speedup_of_auto": arms["static"]["ms_per_step"] / ms,
+            "probe_stats_ms": sms,
+            "cpu_baseline": {"value": tn, "unit": "tuples/s", "cores": cores, "kind": "oracle",
+                             "sample": f"the whole workload; {rn} run(s) with canonical pair sort in {en:.1f} s",
+                             "one_thread": {"value": t1, "unit": "tuples/s", "cores": 1,
+                                            "sample": f"the whole workload; {r1} run(s) in {e1_:.1f} s"}}}
+    print(json.dumps(line))
+    return 0
+
+
 def grid_plans(nb: int, auto_plan):
     """Forced plans timed at one variant-sweep point besides AUTO and STATIC:
     the non-partitioned join, one pass of 6, 8, 10 and 12 radix bits, and two
@@ -1059,6 +1134,8 @@ def main():
         return run_star(args)
     if args.workload == "grid":
         return run_grid(args)
+    if args.workload == "small":
+        return run_small(args)
     return run_eiger(args)
 
 
