@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--log2-rows", type=int, default=28, help="groupby workload: log2 of the rows")
     ap.add_argument("--key-bytes", type=int, choices=[4, 8], default=4, help="wide workload key/payload width")
     ap.add_argument("--batch-joins", type=int, default=4096)
+    ap.add_argument("--batch-log2", default="10,20",
+                    help="batched workload: build rows 2^U(lo,hi), given as lo,hi")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="steps of the separate per-launch profiling pass (stages, roofline)")
     return ap.parse_args()
@@ -546,9 +548,10 @@ def run_eiger(args):
 
 
 def run_batched(args):
-    """4096 independent int32 joins (build 2^U(10,20) rows, probe 4x, per-join
-    skew): one eiger_join_batched call replayed from a CUDA graph, against the
-    same joins as sequential static eiger_join calls."""
+    """Independent int32 joins (default 4096, build 2^U(10,20) rows, probe 4x,
+    per-join skew): one eiger_join_batched call replayed from a CUDA graph,
+    against the same joins with every table in global memory (small joins'
+    shared-memory tables off) and as sequential static eiger_join calls."""
     import torch
 
     from paper_2607_04489_gb300 import eiger, workloads
@@ -557,25 +560,35 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     eiger.load()
-    w = workloads.batched_small(k=args.batch_joins, seed=rank, device=dev)
+    lo, hi = (float(x) for x in args.batch_log2.split(","))
+    w = workloads.batched_small(k=args.batch_joins, log2_lo=lo, log2_hi=hi, seed=rank, device=dev)
     tuples = w.tuples
-    bj = eiger.BatchedJoin(w.builds, w.probes)
-    graph = bj.capture()
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.warmup):
-        graph.replay()
-    sampler = ClockSampler(local).start()
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(args.steps):
-        graph.replay()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    if int(bj.status) != 0 or bj.counts[: bj.k].cpu().tolist() != [p.numel() for p in w.probes]:
-        raise RuntimeError(f"batched join failed: status {int(bj.status)}")
-    ms = e0.elapsed_time(e1) / args.steps
+
+    def time_batch(knobs, steps, sample_clocks=False):
+        bj = eiger.BatchedJoin(w.builds, w.probes, knobs=knobs)
+        graph = bj.capture()
+        for _ in range(args.warmup):
+            graph.replay()
+        sampler = ClockSampler(local).start() if sample_clocks else None
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop() if sampler else None
+        if int(bj.status) != 0 or bj.counts[: bj.k].cpu().tolist() != [p.numel() for p in w.probes]:
+            raise RuntimeError(f"batched join failed: status {int(bj.status)}")
+        return bj, e0.elapsed_time(e1) / steps, clocks
+
+    bj, ms, clocks = time_batch(None, args.steps, sample_clocks=True)
+    # the same batch with every join's table in global memory
+    knobs_global = eiger.BatchKnobs(**{**vars(bj.knobs), "small_rows": 0})
+    _, gms, _ = time_batch(knobs_global, max(1, min(args.steps, 3)))
+    global_only = {"value": tuples / (gms * 1e-3), "unit": "tuples/s", "ms_per_step": gms,
+                   "knobs": vars(knobs_global), "speedup_of_batched": gms / ms}
     # the same joins as sequential static calls, each synchronising for its count
     seq_steps = 0 if args.no_static else max(1, min(args.steps, 2))
     sequential = None
@@ -600,16 +613,19 @@ def run_batched(args):
         sms = e0.elapsed_time(e1) / seq_steps
         sequential = {"value": tuples / (sms * 1e-3), "unit": "tuples/s", "ms_per_step": sms,
                       "speedup_of_batched": sms / ms}
+    lo_s, hi_s = (f"{x:g}" for x in (lo, hi))
     line = {"metric": METRIC, "value": tuples / (ms * 1e-3), "unit": "tuples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"batched: {args.batch_joins} int32 joins, build 2^U(10,20) rows, "
+            "config": {"workload": f"batched: {args.batch_joins} int32 joins, build 2^U({lo_s},{hi_s}) rows, "
                                    "probe 4x build, per-join power-law skew U(0,1); one graph replay",
                        "joins": args.batch_joins, "tuples": tuples,
                        "knobs": vars(bj.knobs) if hasattr(bj.knobs, "__dict__") else str(bj.knobs)},
+            "global_tables_only": global_only,
             "sequential_static": sequential,
             "roofline": batch_roofline(w, ms),
-            "gpu_launches": 4 * args.steps, "clocks": clocks}
+            # setup, the persistent join kernel, the small joins' kernel, status
+            "gpu_launches": (4 if bj.knobs.small_rows > 0 else 3) * args.steps, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
     return 0
@@ -619,8 +635,8 @@ def batch_roofline(w, ms):
     """Compulsory bytes of one replay of the batch (every 4-byte build and
     probe key read once, one 8-byte pair written per match; every probe row of
     this workload matches once) over the whole replay's time, which also holds
-    the batch's three small launches: a lower bound on batch_join's own
-    bandwidth."""
+    the setup and status launches and the small joins' kernel: a lower bound
+    on batch_join's own bandwidth."""
     peaks, src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     nb = sum(int(b.numel()) for b in w.builds)
@@ -629,7 +645,8 @@ def batch_roofline(w, ms):
     gbs = by / (ms * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": "batch_join", "achieved": gbs, "peak": hbm, "peak_source": src,
             "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "algorithmic_bytes": by,
-            "timing": "CUDA events around whole graph replays (batch_join plus three small launches)"}
+            "timing": "CUDA events around whole graph replays (batch_join, batch_small when small "
+                      "joins run in shared memory, and the setup and status launches)"}
 
 
 def profile_pass(step, steps):

@@ -369,7 +369,15 @@ typedef struct {
     int32_t block_threads;   /* 128, 256 or 512                               */
     int32_t chunk_rows;      /* rows per work item: 4096, 16384 or 65536      */
     float load_factor;       /* per-join table load, in (0, 0.9]               */
+    int32_t small_rows;      /* joins with at most this many build rows run   */
+                             /* one CTA per probe chunk, each building the    */
+                             /* join's table in its own shared memory; 0:     */
+                             /* none; at most EIGER_BATCH_SMALL_MAX_I32 (int32 */
+                             /* keys) or EIGER_BATCH_SMALL_MAX_I64 (int64)    */
 } eiger_batch_knobs;
+
+#define EIGER_BATCH_SMALL_MAX_I32 2048
+#define EIGER_BATCH_SMALL_MAX_I64 1024
 
 /*
  * Scratch bytes eiger_join_batched needs for these joins (host copy of the
@@ -386,7 +394,9 @@ eiger_status eiger_join_batched_workspace(const eiger_join_desc* h_descs, int32_
  * fit the L2 cache, Sec. 5.2.2 "medium and small joins"); work items are
  * build chunks and probe chunks of every join, interleaved per join and pulled
  * by a persistent grid, a probe chunk waiting (bounded) until its join's build
- * chunks are in. Join j's matches go to its own outputs in unspecified order;
+ * chunks are in. A join with at most knobs.small_rows build rows takes no
+ * global table: each of its probe chunks is one item that a single CTA runs
+ * whole, with the join's table built in that CTA's shared memory. Join j's matches go to its own outputs in unspecified order;
  * d_counts[j] receives |J_j| (entries beyond capacity are not written).
  * d_descs: k descriptors in device memory. d_counts: k int64, device.
  * d_status: one int32, device: 0 on success, else an eiger_status value

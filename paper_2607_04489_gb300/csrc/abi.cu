@@ -1067,16 +1067,20 @@ eiger_batch_knobs batch_defaults() {
     k.block_threads = 256;
     k.chunk_rows = 16384;
     k.load_factor = 0.5f;
+    k.small_rows = 1024;
     return k;
 }
 
-eiger_status check_batch_knobs(const eiger_batch_knobs& k) {
+eiger_status check_batch_knobs(const eiger_batch_knobs& k, eiger_dtype dtype) {
     if (k.block_threads != 128 && k.block_threads != 256 && k.block_threads != 512)
         return fail(EIGER_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
     if (k.chunk_rows < 1024 || k.chunk_rows > (1 << 20))
         return fail(EIGER_ERR_INVALID_ARG, "chunk_rows must be in [1024, 2^20]");
     if (!(k.load_factor > 0.0f && k.load_factor <= 0.9f))
         return fail(EIGER_ERR_INVALID_ARG, "load_factor outside (0, 0.9]");
+    const int small_max = dtype == EIGER_I32 ? EIGER_BATCH_SMALL_MAX_I32 : EIGER_BATCH_SMALL_MAX_I64;
+    if (k.small_rows < 0 || k.small_rows > small_max)
+        return fail(EIGER_ERR_INVALID_ARG, "small_rows outside [0, %d] for this dtype", small_max);
     return EIGER_OK;
 }
 
@@ -1089,14 +1093,15 @@ extern "C" eiger_status eiger_join_batched_workspace(const eiger_join_desc* h_de
     if (k < 0 || (k > 0 && !h_descs)) return fail(EIGER_ERR_INVALID_ARG, "bad descriptor list");
     if (dtype != EIGER_I32 && dtype != EIGER_I64) return fail(EIGER_ERR_INVALID_ARG, "bad dtype");
     const eiger_batch_knobs kn = knobs ? *knobs : batch_defaults();
-    eiger_status s = check_batch_knobs(kn);
+    eiger_status s = check_batch_knobs(kn, dtype);
     if (s != EIGER_OK) return s;
     unsigned long long slots = 0;
     for (int j = 0; j < k; ++j) {
         const int64_t nb = h_descs[j].nb, np = h_descs[j].np;
         if (nb < 0 || np < 0 || nb > kMaxRows || np > kMaxRows)
             return fail(EIGER_ERR_INVALID_ARG, "join %d: row counts must be in [0, 2^32)", j);
-        if (nb > 0 && np > 0) slots += table_slots(nb, (double)kn.load_factor);
+        // small joins build their tables in shared memory
+        if (nb > 0 && np > 0 && nb > kn.small_rows) slots += table_slots(nb, (double)kn.load_factor);
     }
     Carve c{nullptr, 0};
     batch_layout(c, k, slots, dtype == EIGER_I32 ? 8 : 16);
@@ -1114,7 +1119,7 @@ extern "C" eiger_status eiger_join_batched(eiger_dtype dtype, const eiger_join_d
     if (k > 0 && (!d_descs || !d_counts || !d_workspace))
         return fail(EIGER_ERR_INVALID_ARG, "NULL descriptors, counts or workspace");
     const eiger_batch_knobs kn = knobs ? *knobs : batch_defaults();
-    eiger_status s = check_batch_knobs(kn);
+    eiger_status s = check_batch_knobs(kn, dtype);
     if (s != EIGER_OK) return s;
     const int slot_bytes = dtype == EIGER_I32 ? 8 : 16;
     Carve probe{nullptr, 0};

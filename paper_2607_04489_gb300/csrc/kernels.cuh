@@ -266,6 +266,7 @@ struct BatchLayout {
     unsigned char* ctrl;
     unsigned char* meta;
     unsigned long long* item_prefix;  // [k + 3] item prefix of the k + 2 stages
+    unsigned long long* solo_prefix;  // [k + 1] item prefix of the small joins
     unsigned* built;                  // [k] build rows inserted per join
     unsigned* cleared;                // [k] clear items done per join
     unsigned* dup;                    // [k] 1 when a join's build keys repeat

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libeiger.so")
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_WORKSPACE, ERR_TABLE_FULL, ERR_CUDA, ERR_INTERNAL = range(7)
 I32, I64 = 0, 1
+BATCH_SMALL_MAX_I32, BATCH_SMALL_MAX_I64 = 2048, 1024  # build rows of a shared-memory batch table
 AUTO, NPHJ, PHJ1, PHJ2, STATIC, SMJ = range(6)
 VARIANTS = {"auto": AUTO, "nphj": NPHJ, "phj1": PHJ1, "phj2": PHJ2, "static": STATIC, "smj": SMJ}
 GFUR, GFTR, MAT_AUTO = range(3)
@@ -66,7 +67,7 @@ class JoinDescT(ctypes.Structure):
 
 class BatchKnobsT(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("chunk_rows", ctypes.c_int32),
-                ("load_factor", ctypes.c_float)]
+                ("load_factor", ctypes.c_float), ("small_rows", ctypes.c_int32)]
 
 
 class PlanT(ctypes.Structure):
@@ -670,9 +671,10 @@ class BatchKnobs:
     block_threads: int = 256
     chunk_rows: int = 16384
     load_factor: float = 0.5
+    small_rows: int = 1024  # joins with at most this many build rows use a shared-memory table
 
     def to_c(self) -> BatchKnobsT:
-        return BatchKnobsT(self.block_threads, self.chunk_rows, self.load_factor)
+        return BatchKnobsT(self.block_threads, self.chunk_rows, self.load_factor, self.small_rows)
 
 
 class BatchedJoin:
@@ -767,7 +769,7 @@ def load_tuned_batch_knobs() -> "BatchKnobs | None":
         return None
     k = d.get("knobs", {})
     return BatchKnobs(int(k.get("block_threads", 256)), int(k.get("chunk_rows", 16384)),
-                      float(k.get("load_factor", 0.5)))
+                      float(k.get("load_factor", 0.5)), int(k.get("small_rows", 1024)))
 
 
 # ------------------------------------------------------------------ selector network

@@ -255,12 +255,27 @@ def test_batched_workspace_query_needs_no_gpu(lib):
     for j, (nb, np_) in enumerate([(1000, 4000), (0, 10), (70_000, 5)]):
         descs[j].nb, descs[j].np = nb, np_
     ws = ctypes.c_size_t(0)
-    kn = lib.BatchKnobs().to_c()
-    assert lib.load().eiger_join_batched_workspace(descs, 3, lib.I32, ctypes.byref(kn), ctypes.byref(ws)) == 0
+    so = lib.load()
+    kn = lib.BatchKnobs(small_rows=0).to_c()
+    assert so.eiger_join_batched_workspace(descs, 3, lib.I32, ctypes.byref(kn), ctypes.byref(ws)) == 0
     # tables: 2048 + 0 + 2^18 slots of 8 bytes, plus bookkeeping
     assert ws.value >= (2048 + (1 << 18)) * 8
+    # the 1000-row build is a small join (table in shared memory): no global slots
+    kn = lib.BatchKnobs(small_rows=1000).to_c()
+    assert so.eiger_join_batched_workspace(descs, 3, lib.I32, ctypes.byref(kn), ctypes.byref(ws)) == 0
+    assert (1 << 18) * 8 <= ws.value < (2048 + (1 << 18)) * 8
+    kn = lib.BatchKnobs(small_rows=999).to_c()
+    assert so.eiger_join_batched_workspace(descs, 3, lib.I32, ctypes.byref(kn), ctypes.byref(ws)) == 0
+    assert ws.value >= (2048 + (1 << 18)) * 8
     bad = lib.BatchKnobs(100, 16384, 0.5).to_c()
-    assert lib.load().eiger_join_batched_workspace(descs, 3, lib.I32, ctypes.byref(bad), ctypes.byref(ws)) == lib.ERR_INVALID_ARG
+    assert so.eiger_join_batched_workspace(descs, 3, lib.I32, ctypes.byref(bad), ctypes.byref(ws)) == lib.ERR_INVALID_ARG
+    # shared-memory tables hold at most EIGER_BATCH_SMALL_MAX_* build rows
+    for dt, smax in ((lib.I32, lib.BATCH_SMALL_MAX_I32), (lib.I64, lib.BATCH_SMALL_MAX_I64)):
+        ok = lib.BatchKnobs(small_rows=smax).to_c()
+        assert so.eiger_join_batched_workspace(descs, 3, dt, ctypes.byref(ok), ctypes.byref(ws)) == 0
+        for v in (smax + 1, -1):
+            bad = lib.BatchKnobs(small_rows=v).to_c()
+            assert so.eiger_join_batched_workspace(descs, 3, dt, ctypes.byref(bad), ctypes.byref(ws)) == lib.ERR_INVALID_ARG
     st = ctypes.c_int32(0)
     assert lib.load().eiger_join_batched(lib.I32, None, 3, None, None, None, None, 0, None) == lib.ERR_INVALID_ARG
 

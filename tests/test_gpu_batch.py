@@ -2,7 +2,8 @@
 
 Every join of a batch is compared with the oracle's canonical pairs; the
 cases cover empty joins, single rows, duplicate-heavy keys, int32 and int64
-keys, per-join output capacities smaller than the result, CUDA-graph capture
+keys, small joins whose tables live in shared memory (with the path on and
+off), per-join output capacities smaller than the result, CUDA-graph capture
 and replay, and the status word for an undersized workspace. The full
 4096-join workload is checked by counts (unique build keys, every probe key
 drawn from them: |J_j| = np_j) and by exact parity on sampled joins.
@@ -80,6 +81,72 @@ def test_batched_matches_oracle_per_join(eiger, oracle_mod, dtype, threads, chun
     assert int(bj.status) == 0
     for j in range(len(builds)):
         _check_join(oracle_mod, bj, j, builds[j], probes[j])
+
+
+def _small_batch(dtype, smax, seed, k=48):
+    """Joins around the shared-memory limit of build rows: unique keys with
+    probes drawn from them, duplicate-heavy keys, a handful of all-equal build
+    rows, and random full-width keys; probe sides of one row to a few chunks."""
+    rng = np.random.default_rng(seed)
+    lo, hi = (-2**31, 2**31 - 1) if dtype == np.int32 else (-2**62, 2**62)
+    builds, probes = [], []
+    for j in range(k):
+        nb = int(rng.choice([1, 2, 63, 64, 65, 1000, smax - 1, smax, smax + 1]))
+        np_ = int(rng.choice([1, 100, 4095, 4096, 4097, 9000]))
+        kind = j % 4
+        if kind == 0:
+            bk = rng.permutation(10 * nb)[:nb] * 7 - 5000
+            pk = np.concatenate([bk[rng.integers(0, nb, size=np_ - np_ // 4)], rng.integers(lo, hi, size=np_ // 4)])
+        elif kind == 1:
+            bk = rng.integers(0, max(1, nb // 8), size=nb)
+            pk = rng.integers(0, max(1, nb // 6), size=np_)
+        elif kind == 2:
+            nb = min(nb, 9)
+            bk = np.full(nb, 7)
+            pk = np.where(rng.random(np_) < 0.5, 7, rng.integers(8, 100, size=np_))
+        else:
+            bk = rng.integers(lo, hi, size=nb)
+            pk = np.concatenate([bk[rng.integers(0, nb, size=np_ // 2)], rng.integers(lo, hi, size=np_ - np_ // 2)])
+        builds.append(torch.from_numpy(np.asarray(bk, dtype=dtype)).cuda())
+        probes.append(torch.from_numpy(np.asarray(pk, dtype=dtype)).cuda())
+    return builds, probes
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("small,load", [("max", 0.35), ("max", 0.7), ("none", 0.5)])
+def test_batched_small_joins_shared_memory_tables(eiger, oracle_mod, dtype, small, load):
+    """Small joins (at most small_rows build rows) run one CTA per 4096-row
+    probe chunk with the table in shared memory (at the largest size the
+    table is capped, so a 0.35 load factor runs at 0.5); the same joins with
+    the path off take global tables. Both agree with the oracle join by join."""
+    smax = eiger.BATCH_SMALL_MAX_I32 if dtype == np.int32 else eiger.BATCH_SMALL_MAX_I64
+    builds, probes = _small_batch(dtype, smax, seed=31 + int(load * 100))
+    caps = [oracle_mod.join_count(b.cpu().numpy(), p.cpu().numpy()) for b, p in zip(builds, probes)]
+    knobs = eiger.BatchKnobs(256, 4096, load, smax if small == "max" else 0)
+    bj = eiger.BatchedJoin(builds, probes, capacities=caps, knobs=knobs)
+    bj.run()
+    torch.cuda.synchronize()
+    assert int(bj.status) == 0
+    for j in range(len(builds)):
+        _check_join(oracle_mod, bj, j, builds[j], probes[j])
+
+
+def test_batched_small_joins_graph_replay(eiger, oracle_mod):
+    """A batch of only small joins (64 to 2048 build rows), captured and
+    replayed: every replay redoes each join from its own tables."""
+    from paper_2607_04489_gb300 import workloads
+
+    w = workloads.batched_small(k=256, log2_lo=6, log2_hi=11, seed=12, device="cuda")
+    bj = eiger.BatchedJoin(w.builds, w.probes, knobs=eiger.BatchKnobs(512, 4096, 0.5, eiger.BATCH_SMALL_MAX_I32))
+    g = bj.capture()
+    for _ in range(2):
+        bj.counts.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(bj.status) == 0
+        assert bj.counts.cpu().tolist() == [p.numel() for p in w.probes]
+    for j in range(0, 256, 17):
+        _check_join(oracle_mod, bj, j, w.builds[j], w.probes[j])
 
 
 def test_batched_capacity_caps_each_join(eiger, oracle_mod):
