@@ -50,6 +50,17 @@ def time_knobs(batch: workloads.BatchInput, knobs: eiger.BatchKnobs, reps: int =
     return sorted(times)[len(times) // 2]
 
 
+def pick(grid: list) -> dict:
+    """Sets each entry's objective "rel", the mean over the batches of its time
+    ("ms", one per batch) relative to that batch's fastest entry, and returns
+    the entry with the smallest objective (the first one on ties)."""
+    nb = len(grid[0]["ms"])
+    best_ms = [min(r["ms"][i] for r in grid) for i in range(nb)]
+    for r in grid:
+        r["rel"] = round(sum(x / b for x, b in zip(r["ms"], best_ms)) / nb, 4)
+    return min(grid, key=lambda r: r["rel"])
+
+
 def tune(joins: int = 1024, seeds=(10000, 10001), out: str | None = None) -> dict:
     """Times every knob combination on two kinds of seeded batches: `joins`
     joins of 2^U(10,20) build rows, and 4 * `joins` small joins of 2^U(6,11)
@@ -65,10 +76,7 @@ def tune(joins: int = 1024, seeds=(10000, 10001), out: str | None = None) -> dic
         grid.append({"block_threads": bt, "chunk_rows": ch, "load_factor": lf, "small_rows": sm,
                      "ms": [round(x, 4) for x in ms]})
         torch.cuda.empty_cache()
-    best_ms = [min(r["ms"][i] for r in grid) for i in range(len(batches))]
-    for r in grid:
-        r["rel"] = round(sum(x / b for x, b in zip(r["ms"], best_ms)) / len(batches), 4)
-    best = min(grid, key=lambda r: r["rel"])
+    best = pick(grid)
     result = {
         "version": 3,
         "device": torch.cuda.get_device_name(),

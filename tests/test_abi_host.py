@@ -345,3 +345,21 @@ def test_smj_knob_validation(lib):
     k = lib.Plan("smj", 9, 0, 1).to_c()
     assert so.eiger_join_workspace(100, 100, lib.I64, lib.SMJ, ctypes.byref(k), ctypes.byref(ws)) == 0
     assert so.eiger_join_workspace(100, 100, lib.I64, 6, None, ctypes.byref(ws)) == lib.ERR_INVALID_ARG
+
+
+def test_autotuner_picks_best_mean_relative_time():
+    """The batched autotuner's objective: each entry's time on every tuning
+    batch relative to that batch's fastest entry, averaged; the small batch
+    (sub-millisecond) weighs as much as the large one."""
+    from paper_2607_04489_gb300 import autotune
+
+    grid = [
+        {"small_rows": 0, "ms": [10.0, 0.30]},     # fastest on the large batch by a hair
+        {"small_rows": 2048, "ms": [10.1, 0.15]},  # 1 % slower there, 2x faster on the small one
+        {"small_rows": 1024, "ms": [12.0, 0.15]},
+    ]
+    best = autotune.pick(grid)
+    assert best["small_rows"] == 2048
+    assert [r["rel"] for r in grid] == [1.5, 1.005, 1.1]
+    # ties go to the first entry
+    assert autotune.pick([{"k": 1, "ms": [1.0]}, {"k": 2, "ms": [1.0]}])["k"] == 1
