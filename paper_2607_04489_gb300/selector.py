@@ -6,7 +6,7 @@ join is timed under each of the 15 plan classes (eiger_class_plan), and a
 small network (the library's FP32 kernels, eiger_mlp_*) is trained on the 12
 runtime features (eiger_features) toward the classes near the fastest (a
 soft-target cross-entropy over the measured slowdowns). The exhaustive
-choice (fastest measured class) is the judge; the rule-based selector
+choice (fastest measured class) is the yardstick; the rule-based selector
 (eiger_plan) is the fallback and the comparison.
 
 Pipeline (all steps on the GPU, each writes plain text under selector_data/):
