@@ -212,22 +212,30 @@ __host__ __device__ constexpr size_t smem_gb_bytes(uint32_t tsize, int naggs) {
     return align_up((size_t)(tsize + 1) * sizeof(KeyT), 8) + (size_t)naggs * (tsize + 1) * 8;
 }
 
-// Warp-collective: the lanes with `ok` add their row's aggregates into slot
-// `slot` of the CTA table; lanes sharing a slot are first combined by the
+// Every aggregate's value of row `row` (0 where !ok), loaded together so that
+// the row costs one global-load round trip, not one per aggregate.
+__device__ __forceinline__ void agg_values(const AggSpec& s, bool ok, uint32_t row, long long (&v)[kMaxCols]) {
+#pragma unroll
+    for (int a = 0; a < kMaxCols; ++a) v[a] = (ok && a < s.n) ? agg_value(s, a, row) : 0;
+}
+
+// Warp-collective: the lanes with `ok` add their row's aggregates `v` into
+// slot `slot` of the CTA table; lanes sharing a slot are first combined by the
 // lowest of them (values staged in the warp's scratch), so a hot group costs
 // one shared atomic per warp instead of 32.
 template <typename KeyT>
-__device__ __forceinline__ void warp_aggregate(SmemGb<KeyT>& tab, const AggSpec& s, bool ok, uint32_t slot,
-                                               uint32_t row, long long* scratch) {
+__device__ __forceinline__ void warp_aggregate_vals(SmemGb<KeyT>& tab, const AggSpec& s, bool ok, uint32_t slot,
+                                                    const long long (&v)[kMaxCols], long long* scratch) {
     const unsigned lane = lane_id();
     const unsigned peers = __match_any_sync(0xffffffffu, ok ? slot : 0xFFFFFFFFu);
     const bool leader = ok && (int)lane == __ffs(peers) - 1;
-    for (int a = 0; a < s.n; ++a) {
-        const long long v = ok ? agg_value(s, a, row) : 0;
-        scratch[lane] = v;
+#pragma unroll
+    for (int a = 0; a < kMaxCols; ++a) {
+        if (a >= s.n) break;
+        scratch[lane] = v[a];
         __syncwarp();
         if (leader) {
-            long long acc = v;
+            long long acc = v[a];
             unsigned m = peers & ~(1u << lane);
             while (m) {
                 const int l = __ffs(m) - 1;
@@ -238,6 +246,14 @@ __device__ __forceinline__ void warp_aggregate(SmemGb<KeyT>& tab, const AggSpec&
         }
         __syncwarp();
     }
+}
+
+template <typename KeyT>
+__device__ __forceinline__ void warp_aggregate(SmemGb<KeyT>& tab, const AggSpec& s, bool ok, uint32_t slot,
+                                               uint32_t row, long long* scratch) {
+    long long v[kMaxCols];
+    agg_values(s, ok, row, v);
+    warp_aggregate_vals(tab, s, ok, slot, v, scratch);
 }
 
 template <typename InKey, typename KeyT>
@@ -482,19 +498,35 @@ __global__ void __launch_bounds__(kGbThreads)
         const uint32_t pend = a.start[p + 1];
         const unsigned long long beg = (unsigned long long)a.start[p] + c * kGbChunk;
         const unsigned long long end = beg + kGbChunk < pend ? beg + kGbChunk : pend;
+        // each round's key and values are loaded one round ahead, so their
+        // round trip overlaps the previous round's table updates
+        KeyT kn{};
+        long long vn[kMaxCols];
+        {
+            const bool okn = beg + threadIdx.x < end;
+            if (okn) kn = __ldcs(a.key + (uint32_t)(beg + threadIdx.x));
+            agg_values(a.s, okn, (uint32_t)(beg + threadIdx.x), vn);
+        }
         for (unsigned long long base = beg; base < end; base += kGbThreads) {
-            const uint32_t r = (uint32_t)(base + threadIdx.x);
             bool ok = base + threadIdx.x < end;
+            const KeyT k = kn;
+            long long v[kMaxCols];
+#pragma unroll
+            for (int q = 0; q < kMaxCols; ++q) v[q] = vn[q];
+            const unsigned long long nx = base + kGbThreads + threadIdx.x;
+            const bool okn = nx < end;
+            if (okn) kn = __ldcs(a.key + (uint32_t)nx);
+            agg_values(a.s, okn, (uint32_t)nx, vn);
             uint32_t slot = 0;
             if (ok) {
-                slot = tab.slot_of(__ldcs(a.key + r));
+                slot = tab.slot_of(k);
                 if (slot == tab.tsize) s_special = 1;
                 if (slot == 0xFFFFFFFFu) {
                     s_full = 1;
                     ok = false;
                 }
             }
-            warp_aggregate(tab, a.s, ok, slot, r, scratch);
+            warp_aggregate_vals(tab, a.s, ok, slot, v, scratch);
         }
         __syncthreads();
         if (s_full) {  // more groups than one table: the host repartitions with more bits
